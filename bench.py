@@ -1,0 +1,357 @@
+"""Benchmark of the matrix-free multivector product Y = A X on GB300.
+
+One step = one fe_apply over the whole workload (gather, sum-factorised
+contractions, quadrature-point operation, transposed contractions,
+colour-ordered assembly).  Default workload: the 32^3-cell periodic box,
+p = 6, n_q = 8, n_vec = 64 (7,077,888 DoFs), FP64, with FP32 measured beside
+it.  Inputs (3.6 GB per block in FP64) are far larger than L2, so no flush is
+needed between steps.
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank applies its own copy
+of the workload on its own GPU (weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2208_07129_gb300 import inputs  # noqa: E402
+
+METRIC = "FE A·X GDoF-vectors/s, FP64 vs mixed (rel err ≤1e-6), % roofline; PCG time"
+UNIT = "GDoF-vectors/s"
+
+# Roofline denominators.  HBM: measured copy bandwidth.  ALU-bound kernels: the
+# pipe's unit count times the maximum SM clock (GB300: 152 SMs; per SM and clock
+# 2 FP64 FMA lanes -- a DFMA microbenchmark measured 1.19 TFLOP/s -- and 128 FP32
+# FMA lanes), see the design doc.
+SMS = 152
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tflops(dtype: str, sm_max_mhz: float) -> float:
+    lanes = {"f64": 2, "f32": 128}[dtype]
+    return SMS * lanes * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def flops_per_cell_vec(np_: int, nq: int) -> int:
+    """Algorithmic flops per cell and vector: 2 flops per multiply-add of the six
+    N / N^T passes and six D~ / D~^T passes (Sec. 2.2 complexity), plus 16 per
+    point for the quadrature-point operation (symmetric 3x3 apply: 15, value: 1)."""
+    return 4 * (np_ ** 3 * nq + np_ ** 2 * nq ** 2 + np_ * nq ** 3) + 12 * nq ** 4 + 16 * nq ** 3
+
+
+def bytes_per_apply(w, elem: int) -> int:
+    """Algorithmic HBM bytes: X read once, Y written once, V coefficient per point
+    (8 B), and per-point metric (6 values) on trilinear meshes."""
+    nq3 = w.nq ** 3
+    geo = w.num_cells * nq3 * elem * (7 if w.perturb_seed is not None else 1)
+    return w.num_dofs * w.n_vec * 2 * elem + geo
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, sm_max_default: float):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": sm_max_default, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": sm_max_default, "reasons": ["unsampled"]}
+        load = [r for r in rows if r[2] > 300.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(load), "reasons": reasons}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_for(kernel: str, source_files):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel's sources are unchanged since that capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    data = json.load(open(p))
+    ent = data.get(kernel)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for f in source_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if ent.get("source_sha256") != h.hexdigest():
+        return None
+    return ent.get("dram_bytes_per_launch_full")
+
+
+KERNEL_SOURCES = ["paper_2208_07129_gb300/csrc/fe_cell_kernel.cuh", "paper_2208_07129_gb300/csrc/fe_dispatch.cuh"]
+
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    """The FP64 oracle as it stands, on the host cores: rows of A X for this
+    workload, each row assembled from its cell matrices and multiplied with X."""
+    from oracle import oracle as orc
+    mesh = orc.Mesh(w.nx, w.ny, w.nz, periodic=w.periodic, vertices=w.vertices())
+    Vo = w.potential_at(orc.quad_points(mesh, w.p, w.nq))
+    rng = np.random.default_rng(0)
+    n = w.num_dofs
+    X = inputs.random_block(n, w.n_vec, w.x_dist, w.x_seed)
+    probe = np.sort(rng.integers(0, n, 8 * orc.num_threads()))
+    t0 = time.perf_counter()
+    orc.apply_rows(mesh, w.p, w.nq, X, probe, Vq=Vo, mu=w.mu)
+    dt = time.perf_counter() - t0
+    rows_n = max(len(probe), int(len(probe) * budget_s / max(dt, 1e-3)))
+    rows = np.sort(rng.integers(0, n, rows_n))
+    t0 = time.perf_counter()
+    orc.apply_rows(mesh, w.p, w.nq, X, rows, Vq=Vo, mu=w.mu)
+    dt = time.perf_counter() - t0
+    return {"value": len(rows) * w.n_vec / dt / 1e9, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{len(rows)} of {n} rows of A X ({w.name}), each row assembled from its cell matrices "
+                      f"by FP64 quadrature and multiplied with the {w.n_vec}-vector block; {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    w = inputs.WORKLOADS["c2"]
+    per_step = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
+        if s >= args.warmup:
+            per_step.append(cb["value"])
+    v = statistics.median(per_step)
+    cb["value"] = v
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": w.name, "dofs": w.num_dofs, "n_vec": w.n_vec},
+                      "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                                  "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def time_mode(fe, torch, ctx, w, mode, steps, warmup, world):
+    """Device-timed applies (CUDA events on the launching stream) and per-launch
+    duration of the cell kernel; returns (ms_per_step, launches_per_step)."""
+    fe.fe_set_mode(ctx, mode)
+    dt = torch.float64 if mode == "fp64" else torch.float32
+    X = torch.from_numpy(w.make_x()).to(device="cuda", dtype=dt)
+    Y = torch.empty_like(X)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fe.fe_apply(ctx, X, Y)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        fe.fe_apply(ctx, X, Y)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total = ev[0].elapsed_time(ev[steps])
+    ms = max_over_ranks(total / steps, world)
+    return ms, per, X, Y
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2208_07129_gb300 import build, fe
+    if rank == 0:
+        build.build()
+    barrier(world)
+    fe.lib()
+    peaks, peak_src = measured_peaks()
+    w = inputs.WORKLOADS[args.workload]
+    ctx = fe.setup_workload(w)
+    n_colors = 8 if (w.periodic is False or all(n % 2 == 0 for n in (w.nx, w.ny, w.nz))) else 27
+    f_cell = flops_per_cell_vec(w.p + 1, w.nq)
+    flops = f_cell * w.num_cells * w.n_vec
+    units = w.num_dofs * w.n_vec
+
+    modes = {}
+    with ClockSampler(local) as clk:
+        ms64, per64, X64, Y64 = time_mode(fe, torch, ctx, w, "fp64", args.steps, max(3, args.warmup), world)
+        ms32, per32, X32, Y32 = time_mode(fe, torch, ctx, w, "fp32", args.steps, max(3, args.warmup), world)
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+
+    # end to end through the public host-buffer call: H2D of X, apply, D2H of Y
+    fe.fe_set_mode(ctx, "fp64")
+    Xh = X64.cpu().pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
+    fe.fe_apply_host(ctx, Xh, Yh)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_steps = max(2, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        fe.fe_apply_host(ctx, Xh, Yh)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+
+    # accuracy of both modes on sampled rows against the FP64 oracle
+    acc = {}
+    if rank == 0 and not args.no_cpu:
+        from oracle import oracle as orc
+        mesh = orc.Mesh(w.nx, w.ny, w.nz, periodic=w.periodic, vertices=w.vertices())
+        Vo = w.potential_at(orc.quad_points(mesh, w.p, w.nq))
+        rows = np.sort(np.random.default_rng(1).integers(0, w.num_dofs, 48))
+        ridx = torch.from_numpy(rows).cuda()
+        for mode, Xd, Yd in (("fp64", X64, Y64), ("fp32", X32, Y32)):
+            Xr = Xd.double().cpu().numpy()
+            Yref = orc.apply_rows(mesh, w.p, w.nq, Xr, rows, Vq=Vo, mu=w.mu)
+            Yg = Yd[ridx].double().cpu().numpy()
+            acc[mode] = float(np.linalg.norm(Yg - Yref) / np.linalg.norm(Yref))
+            del Xr
+
+    hbm = peaks["hbm_gbs"]
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    total_units = units * world
+    value = total_units / (ms64 * 1e-3) / 1e9
+    value32 = total_units / (ms32 * 1e-3) / 1e9
+    # dominant kernel: the cell kernel, n_colors launches per step; achieved =
+    # algorithmic flops per launch / mean launch duration (event-timed step / launches)
+    ach64 = flops / (ms64 * 1e-3) / 1e12
+    ach32 = flops / (ms32 * 1e-3) / 1e12
+    pk64 = alu_peak_tflops("f64", sm_max)
+    pk32 = alu_peak_tflops("f32", sm_max)
+    b64 = bytes_per_apply(w, 8)
+    b32 = bytes_per_apply(w, 4)
+    traffic = traffic_for("cell_apply_kernel<double,7,8,false>", KERNEL_SOURCES)
+    modes["fp32"] = {
+        "value": value32, "unit": UNIT, "ms_per_step": ms32, "dtype": "f32",
+        "rel_err_vs_oracle": acc.get("fp32"),
+        "roofline": {"bound": "alu", "achieved": ach32, "peak": pk32, "unit": "TFLOP/s", "frac": ach32 / pk32,
+                     "hbm_frac": b32 / (ms32 * 1e-3) / 1e9 / hbm,
+                     "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x max SM clock"},
+    }
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "dofs": w.num_dofs, "cells": w.num_cells, "p": w.p, "n_q": w.nq,
+                   "n_vec": w.n_vec, "l2": "inputs larger than L2 (3.6 GB per FP64 block), no flush",
+                   "rel_err_vs_oracle": acc.get("fp64"), "sampled_rows": 48},
+        "roofline": {"bound": "alu", "achieved": ach64, "peak": pk64, "unit": "TFLOP/s", "frac": ach64 / pk64,
+                     "traffic": traffic, "hbm_frac": b64 / (ms64 * 1e-3) / 1e9 / hbm,
+                     "kernel": "cell_apply_kernel<double,7,8,false>",
+                     "peak_source": f"152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_max:.0f} MHz; HBM {hbm} GB/s {peak_src}"},
+        "modes": modes,
+        "e2e": {"value": total_units / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": units * 8,
+                "d2h_bytes_per_step": units * 8},
+        "gpu_launches": n_colors * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    fe.fe_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

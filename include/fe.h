@@ -1,0 +1,142 @@
+/*
+ * fe.h -- C ABI of libfe: matrix-free multivector products Y = A X for the
+ * finite-element operator A = -mu lap + V(x) on a structured hexahedral mesh,
+ * degree-p Lagrange elements on Gauss-Lobatto-Legendre nodes, run by
+ * hand-written CUDA kernels for sm_103a (GB300).
+ *
+ * Operation (paper: Sec. 2.1 stiffness / mass integrals; Sec. 2.2 the
+ * decomposition V = A U = sum_e Q^T A^(e) Q U under the constraints C; the
+ * cell products of Algorithm 2, executed batch-wise as in Algorithm 4):
+ *
+ *   A_IJ = sum_e sum_Q w_Q det J [ mu (J^-T grad N_I).(J^-T grad N_J) + V(x_Q) N_I N_J ]
+ *
+ * with the tensor n_q-point quadrature rule (Gauss or GLL).
+ *
+ * Conventions shared by every call:
+ *  - Multivectors are DoF-major and vector-contiguous (the paper's batched
+ *    contiguous layout, Sec. 3.2.1, with one batch holding all n_vec
+ *    vectors): element (dof, v) lives at X[dof * n_vec + v].  The dtype is
+ *    double in FE_FP64 mode and float in every other mode.
+ *  - Global node (gx, gy, gz) has index gx + Nx (gy + Ny gz), where Nx = nx p + 1
+ *    for a Dirichlet box and Nx = nx p for a periodic box (wrap-around).
+ *  - Cells are e = cx + nx (cy + ny cz); quadrature points Q = q1 + n_q (q2 + n_q q3).
+ *  - Dirichlet (FE_BC_DIRICHLET0): the operator is P A P, P zeroing the boundary
+ *    nodes (Sec. 3.2.2: Dirichlet constraints have no master nodes).  Boundary
+ *    entries of X are ignored (read as 0) and boundary rows of Y are written 0.
+ *  - Device pointers are caller-owned CUDA device memory unless the name says
+ *    "host".  Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) unless stated otherwise.
+ *  - No call aborts.  Invalid arguments return FE_EINVAL before any launch;
+ *    CUDA errors return FE_ECUDA.  Errors raised by asynchronous device work
+ *    surface at the next call or through fe_last_device_status().
+ */
+#ifndef FE_H_
+#define FE_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe_ctx fe_ctx;
+
+typedef enum {
+  FE_OK = 0,
+  FE_EINVAL = 1,        /* invalid argument, detected before any launch */
+  FE_ENOMEM = 2,        /* host or device allocation failed */
+  FE_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+  FE_ENOTCONV = 4,      /* iterative solve stopped before reaching rtol */
+  FE_EBREAKDOWN = 5,    /* Krylov breakdown (p^T A p <= 0 or r^T z <= 0) */
+  FE_ENONFINITE = 6,    /* NaN or Inf met in a result */
+  FE_ETIMEOUT = 7,      /* a bounded device wait gave up */
+  FE_EUNSUPPORTED = 8   /* valid request outside the compiled kernel set */
+} fe_status;
+
+typedef enum { FE_BC_DIRICHLET0 = 0, FE_BC_PERIODIC = 1 } fe_bc;
+typedef enum { FE_QUAD_GAUSS = 0, FE_QUAD_GLL = 1 } fe_quad_kind;
+
+/* Arithmetic of the cell kernels.  FE_FP64: double data, double arithmetic.
+ * FE_FP32: float data, float arithmetic on CUDA cores.  FE_TF32 / FE_BF16:
+ * float data, the sum-factorised contractions on tensor cores with FP32
+ * accumulation (operands rounded to TF32 / BF16); the quadrature-point
+ * operation stays FP32.  Geometry is always computed in FP64. */
+typedef enum { FE_FP64 = 0, FE_FP32 = 1, FE_TF32 = 2, FE_BF16 = 3 } fe_mode;
+
+typedef struct {
+  int nx, ny, nz;          /* cells per direction, >= 1 (>= 2 when periodic) */
+  double lo[3], hi[3];     /* box corners (used when vertex_xyz == NULL) */
+  int bc;                  /* fe_bc */
+  const double* vertex_xyz;/* host, optional: (nx+1)(ny+1)(nz+1) x 3 vertex
+                              coordinates, x fastest; each cell is the trilinear
+                              image of [-1,1]^3 and gets per-point Jacobians.
+                              Copied during fe_setup. */
+} fe_mesh_desc;
+
+typedef struct {
+  int n_q;                 /* points per direction; p+1 <= n_q <= p+3 */
+  int kind;                /* fe_quad_kind */
+} fe_quad_desc;
+
+/* Build the operator for degree p (1..8) on `mesh` with quadrature `quad`
+ * and diffusion coefficient mu (the paper's mu; 1/2 for -1/2 lap).  The
+ * potential starts at V = 0 (see fe_set_potential).  Computes in FP64 on the
+ * host: GLL nodes, quadrature, the 1D shape-value matrix N (n_q x n_p) and the
+ * collocation derivative matrix D~ (n_q x n_q) of Sec. 2.2, the Jacobians at
+ * every quadrature point (rejecting det J <= 0 with FE_EINVAL), the metric
+ * terms mu det J J^-1 J^-T of the cell stiffness, and the cell colouring used
+ * for conflict-free assembly; then uploads them.  *out receives an opaque
+ * handle owned by the caller (free with fe_destroy).  Synchronous. */
+fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_desc* quad, double mu, fe_ctx** out);
+
+/* Release everything the context owns.  NULL is allowed. */
+void fe_destroy(fe_ctx* ctx);
+
+/* Stored DoFs (boundary nodes included) and cells. */
+size_t fe_num_dofs(const fe_ctx* ctx);
+size_t fe_num_cells(const fe_ctx* ctx);
+int fe_num_quad_points_1d(const fe_ctx* ctx);
+
+/* Physical coordinates of every quadrature point: xyz_host[(e n_q^3 + Q) 3 + d],
+ * caller-owned host buffer of E n_q^3 3 doubles.  Synchronous. */
+fe_status fe_quadrature_points(const fe_ctx* ctx, double* xyz_host);
+
+/* Set V at the quadrature points: Vq_host[e n_q^3 + Q] (host, FP64, E n_q^3
+ * values; NULL sets V = 0).  The product det J w_Q V(x_Q) of the weighted mass
+ * (Sec. 2.2, the diagonal G of M^kappa = N^T G N) is formed in FP64 and
+ * uploaded.  Synchronous. */
+fe_status fe_set_potential(fe_ctx* ctx, const double* Vq_host);
+
+/* Select the arithmetic mode of later fe_apply calls (default FE_FP64). */
+fe_status fe_set_mode(fe_ctx* ctx, fe_mode mode);
+fe_mode fe_get_mode(const fe_ctx* ctx);
+
+/* Y = A X for n_vec >= 0 vectors (Algorithm 2 per cell, batched over cells and
+ * vector blocks as in Algorithm 4, assembled without atomics by cell colours).
+ * X, Y: device, num_dofs x n_vec, dtype of the current mode, X != Y (no
+ * overlap).  Y is overwritten, never accumulated.  Asynchronous on stream. */
+fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream);
+
+/* Same product with HOST buffers: copies X_host to library-owned device
+ * staging memory, applies, copies the result to Y_host and synchronises the
+ * stream.  For pinned host buffers the copies are asynchronous DMA.  The
+ * staging memory is kept in the context for reuse. */
+fe_status fe_apply_host(fe_ctx* ctx, const void* X_host, void* Y_host, int n_vec, void* stream);
+
+/* diag(A) as a device FP64 vector of num_dofs entries (constrained rows get 1,
+ * the convention of the Jacobi preconditioner), computed matrix-free from the
+ * same tables: A_II = sum over cells containing I of A^(e)_ii. */
+fe_status fe_diagonal(fe_ctx* ctx, double* diag, void* stream);
+
+/* Status word written by asynchronous device work (non-finite values met,
+ * bounded waits that gave up); reading it synchronises the context's work and
+ * clears it. */
+fe_status fe_last_device_status(fe_ctx* ctx);
+
+const char* fe_status_str(fe_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE_H_ */

@@ -1,0 +1,98 @@
+// Internal types of libfe shared by the host setup, the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/fe.h"
+
+namespace fe {
+
+constexpr int kMaxP = 8;
+constexpr int kMaxNQ = kMaxP + 3;
+
+// Structured-mesh description as the kernels see it.
+struct MeshDev {
+  int nx, ny, nz;     // cells
+  int Nx, Ny, Nz;     // stored nodes per direction
+  int periodic;       // 1: wrap-around numbering
+  int cx_col, cy_col; // colours per direction in x and y (2 or 3); colour
+                      // index = kx + cx_col (ky + cy_col kz)
+  int last_odd_x, last_odd_y, last_odd_z;  // periodic with odd n: last cell takes colour 2
+};
+
+// 1D tables with the square roots of the quadrature weights folded in
+// (Sec. 3.2.4: N(q,i) <- N(q,i) sqrt(w_q), D~(q1,q2) <- D~(q1,q2) sqrt(w_q1/w_q2)),
+// so that the quadrature-point operation needs no weights.  Passed by value
+// as a kernel parameter (constant bank) so every contraction reads its
+// coefficients as uniform constant operands.
+template <typename T, int NP, int NQ>
+struct Tables {
+  T N[NQ][NP];
+  T D[NQ][NQ];
+};
+
+// Geometry of the quadrature-point operation.  With weights folded into the
+// tables:  G_sd = mu det J (J^-1 J^-T)_sd   and   c = det J V.
+// Affine cells: one G per cell (cellG[e*6 + k], k = 00,01,02,11,12,22).
+// General (trilinear) cells: ptG[(e*6 + k) * nq3 + Q].  Always ptC[e*nq3 + Q].
+template <typename T>
+struct Geom {
+  const T* cellG;
+  const T* ptG;
+  const T* ptC;
+};
+
+struct ColorSet {
+  int n_colors;
+  std::vector<int> offset;  // n_colors + 1
+};
+
+struct KernelLaunch {
+  const int* cells;   // cell ids of this colour (device)
+  int n_cells;
+  int n_vec;
+  int vb;             // vectors per CTA
+  int nty;            // lines in flight per CTA (blockDim.y)
+  cudaStream_t stream;
+};
+
+}  // namespace fe
+
+struct fe_ctx {
+  // mesh and discretisation
+  int nx, ny, nz, periodic, p, np, nq, quad_kind;
+  double mu;
+  int general;                 // 1: per-point metric (trilinear cells)
+  size_t n_dofs, n_cells;
+  fe::MeshDev mdev;
+  // host FP64 data
+  std::vector<double> gll, qx, qw, N1, D1;   // N1[q*np+i], D1[q*nq+k] (unfolded)
+  std::vector<double> Nf, Df;                // folded
+  std::vector<double> vertices;              // copy of the vertex array (general)
+  double box_lo[3] = {0, 0, 0}, box_h[3] = {1, 1, 1};  // uniform box: corner and cell size
+  std::vector<double> detJ;                  // per point (E*nq3)
+  std::vector<double> cellG, ptG;            // FP64 metric (affine / general)
+  std::vector<int> cells_by_color;
+  fe::ColorSet colors;
+  // device data
+  int* d_cells = nullptr;
+  double *d_cellG64 = nullptr, *d_ptG64 = nullptr, *d_ptC64 = nullptr;
+  float *d_cellG32 = nullptr, *d_ptG32 = nullptr, *d_ptC32 = nullptr;
+  double* d_detJ = nullptr;
+  int* d_status = nullptr;
+  // staging for fe_apply_host
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  fe_mode mode = FE_FP64;
+  // launch shape per mode (vectors per CTA, lines per CTA)
+  int vb64 = 8, nty64 = 16, vb32 = 32, nty32 = 8;
+};
+
+namespace fe {
+// Kernel dispatch (defined in the kernel translation units).
+cudaError_t apply_cc_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s);
+cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);
+cudaError_t diagonal_f64(const fe_ctx* c, double* diag, cudaStream_t s);
+}  // namespace fe

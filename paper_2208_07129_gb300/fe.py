@@ -1,0 +1,209 @@
+"""Python binding of libfe (include/fe.h).
+
+The functions carry the C names and do argument marshalling only: every step
+of the operator runs inside libfe's CUDA kernels.  Device buffers are torch
+CUDA tensors (PyTorch provides memory and streams); host arrays are numpy.
+The library must have been built (``paper_2208_07129_gb300.build``): there is
+no fallback, and a missing or unloadable libfe.so raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfe.so")
+
+FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOTCONV, FE_EBREAKDOWN, FE_ENONFINITE, FE_ETIMEOUT, FE_EUNSUPPORTED = range(9)
+FE_BC_DIRICHLET0, FE_BC_PERIODIC = 0, 1
+FE_QUAD_GAUSS, FE_QUAD_GLL = 0, 1
+FE_FP64, FE_FP32, FE_TF32, FE_BF16 = 0, 1, 2, 3
+MODES = {"fp64": FE_FP64, "fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16}
+
+
+class FeError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+
+
+class fe_mesh_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("bc", ctypes.c_int), ("vertex_xyz", ctypes.POINTER(ctypes.c_double))]
+
+
+class fe_quad_desc(ctypes.Structure):
+    _fields_ = [("n_q", ctypes.c_int), ("kind", ctypes.c_int)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfe.so (raises if it is missing: the product path has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libfe.so not built at {LIB_PATH}; run paper_2208_07129_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "fe_setup": (ctypes.c_int, [ctypes.POINTER(fe_mesh_desc), ctypes.c_int, ctypes.POINTER(fe_quad_desc),
+                                    ctypes.c_double, ctypes.POINTER(_VP)]),
+        "fe_destroy": (None, [_VP]),
+        "fe_num_dofs": (ctypes.c_size_t, [_VP]),
+        "fe_num_cells": (ctypes.c_size_t, [_VP]),
+        "fe_num_quad_points_1d": (ctypes.c_int, [_VP]),
+        "fe_quadrature_points": (ctypes.c_int, [_VP, _DP]),
+        "fe_set_potential": (ctypes.c_int, [_VP, _DP]),
+        "fe_set_mode": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "fe_get_mode": (ctypes.c_int, [_VP]),
+        "fe_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+        "fe_apply_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+        "fe_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
+        "fe_last_device_status": (ctypes.c_int, [_VP]),
+        "fe_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_str(s: int) -> str:
+    try:
+        return lib().fe_status_str(int(s)).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(status: int, what: str):
+    if status != FE_OK:
+        raise FeError(status, what)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def fe_setup(nx: int, ny: int, nz: int, p: int, n_q: int, *, periodic: bool = False,
+             lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), vertices: Optional[np.ndarray] = None,
+             quad: int = FE_QUAD_GAUSS, mu: float = 0.5) -> int:
+    md = fe_mesh_desc()
+    md.nx, md.ny, md.nz = nx, ny, nz
+    for d in range(3):
+        md.lo[d] = float(lo[d])
+        md.hi[d] = float(hi[d])
+    md.bc = FE_BC_PERIODIC if periodic else FE_BC_DIRICHLET0
+    keep = None
+    if vertices is not None:
+        keep = np.ascontiguousarray(vertices, dtype=np.float64)
+        if keep.size != (nx + 1) * (ny + 1) * (nz + 1) * 3:
+            raise ValueError("vertices must hold (nx+1)(ny+1)(nz+1) x 3 coordinates")
+        md.vertex_xyz = keep.ctypes.data_as(_DP)
+    qd = fe_quad_desc(n_q, quad)
+    out = _VP()
+    _check(lib().fe_setup(ctypes.byref(md), p, ctypes.byref(qd), mu, ctypes.byref(out)), "fe_setup")
+    return out.value
+
+
+def fe_destroy(ctx: int) -> None:
+    lib().fe_destroy(ctx)
+
+
+def fe_num_dofs(ctx: int) -> int:
+    return int(lib().fe_num_dofs(ctx))
+
+
+def fe_num_cells(ctx: int) -> int:
+    return int(lib().fe_num_cells(ctx))
+
+
+def fe_num_quad_points_1d(ctx: int) -> int:
+    return int(lib().fe_num_quad_points_1d(ctx))
+
+
+def fe_quadrature_points(ctx: int) -> np.ndarray:
+    E, nq = fe_num_cells(ctx), fe_num_quad_points_1d(ctx)
+    out = np.zeros((E, nq ** 3, 3))
+    _check(lib().fe_quadrature_points(ctx, out.ctypes.data_as(_DP)), "fe_quadrature_points")
+    return out
+
+
+def fe_set_potential(ctx: int, Vq: Optional[np.ndarray]) -> None:
+    if Vq is None:
+        _check(lib().fe_set_potential(ctx, None), "fe_set_potential")
+        return
+    E, nq = fe_num_cells(ctx), fe_num_quad_points_1d(ctx)
+    v = np.ascontiguousarray(Vq, dtype=np.float64).reshape(-1)
+    if v.size != E * nq ** 3:
+        raise ValueError("Vq must hold E * n_q^3 values")
+    _check(lib().fe_set_potential(ctx, v.ctypes.data_as(_DP)), "fe_set_potential")
+
+
+def fe_set_mode(ctx: int, mode) -> None:
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(lib().fe_set_mode(ctx, m), "fe_set_mode")
+
+
+def fe_get_mode(ctx: int) -> int:
+    return int(lib().fe_get_mode(ctx))
+
+
+def _check_block(ctx: int, t, what: str):
+    import torch
+    mode = fe_get_mode(ctx)
+    want = torch.float64 if mode == FE_FP64 else torch.float32
+    if not t.is_cuda or t.dtype != want or not t.is_contiguous() or t.dim() != 2 or t.shape[0] != fe_num_dofs(ctx):
+        raise ValueError(f"{what}: need a contiguous CUDA {want} tensor of shape (num_dofs, n_vec)")
+
+
+def fe_apply(ctx: int, X, Y, stream=None) -> None:
+    """Y = A X on the device (torch tensors, DoF-major (num_dofs, n_vec))."""
+    _check_block(ctx, X, "X")
+    _check_block(ctx, Y, "Y")
+    if X.shape != Y.shape:
+        raise ValueError("X and Y must have the same shape")
+    _check(lib().fe_apply(ctx, X.data_ptr(), Y.data_ptr(), X.shape[1], _stream_ptr(stream)), "fe_apply")
+
+
+def fe_apply_host(ctx: int, X, Y, stream=None) -> None:
+    """Y = A X with host buffers (pinned torch CPU tensors or numpy arrays)."""
+    import torch
+    def ptr(a):
+        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+    n_vec = X.shape[1]
+    _check(lib().fe_apply_host(ctx, ptr(X), ptr(Y), n_vec, _stream_ptr(stream)), "fe_apply_host")
+
+
+def fe_diagonal(ctx: int, diag, stream=None) -> None:
+    import torch
+    if not diag.is_cuda or diag.dtype != torch.float64 or diag.numel() != fe_num_dofs(ctx):
+        raise ValueError("diag must be a CUDA float64 tensor with num_dofs entries")
+    _check(lib().fe_diagonal(ctx, diag.data_ptr(), _stream_ptr(stream)), "fe_diagonal")
+
+
+def fe_last_device_status(ctx: int) -> int:
+    return int(lib().fe_last_device_status(ctx))
+
+
+def setup_workload(w, mu: Optional[float] = None) -> int:
+    """fe_setup + fe_set_potential for an ``inputs.Workload`` (V evaluated at
+    the library's own quadrature points)."""
+    ctx = fe_setup(w.nx, w.ny, w.nz, w.p, w.nq, periodic=w.periodic, vertices=w.vertices(),
+                   mu=w.mu if mu is None else mu)
+    V = w.potential_at(fe_quadrature_points(ctx))
+    if V is not None:
+        fe_set_potential(ctx, V)
+    return ctx

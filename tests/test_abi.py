@@ -1,0 +1,70 @@
+"""The C ABI library loads, exports every symbol declared in include/*.h, and
+rejects invalid arguments on the host before touching a GPU.  CPU only."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libfe():
+    from paper_2208_07129_gb300 import build, fe
+    build.build()
+    return fe.lib()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(fe_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_headers_declare_the_boundary():
+    names = declared_symbols()
+    for must in ("fe_setup", "fe_apply", "fe_destroy", "fe_set_potential", "fe_apply_host"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(libfe):
+    missing = [n for n in declared_symbols() if not hasattr(libfe, n)]
+    assert not missing, missing
+
+
+def test_status_strings(libfe):
+    from paper_2208_07129_gb300 import fe
+    assert fe.status_str(fe.FE_OK) == "ok"
+    assert "invalid" in fe.status_str(fe.FE_EINVAL)
+    assert fe.status_str(99) == "unknown status"
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(nx=0, ny=2, nz=2, p=2, n_q=4), 1),                       # no cells
+    (dict(nx=2, ny=2, nz=2, p=9, n_q=11), 8),                      # degree outside the compiled set
+    (dict(nx=2, ny=2, nz=2, p=4, n_q=4), 8),                       # n_q < p + 1
+    (dict(nx=2, ny=2, nz=2, p=4, n_q=8), 8),                       # n_q > p + 3
+    (dict(nx=1, ny=2, nz=2, p=2, n_q=4, periodic=True), 1),        # periodic needs >= 2 cells
+    (dict(nx=2, ny=2, nz=2, p=2, n_q=4, lo=(0, 0, 0), hi=(1, 0, 1)), 1),  # empty box
+])
+def test_setup_rejects_before_any_launch(libfe, kw, status):
+    from paper_2208_07129_gb300 import fe
+    with pytest.raises(fe.FeError) as ei:
+        ctx = fe.fe_setup(**kw)
+        fe.fe_destroy(ctx)
+    assert ei.value.status == status
+
+
+def test_null_arguments(libfe):
+    VP = ctypes.c_void_p
+    assert libfe.fe_apply(None, None, None, 1, None) == 1
+    assert libfe.fe_setup(None, 2, None, 0.5, None) == 1
+    assert libfe.fe_num_dofs(None) == 0
+    libfe.fe_destroy(None)

@@ -1,0 +1,197 @@
+"""GPU parity of fe_apply against the FP64 oracle, through the C ABI.
+
+Small meshes are compared element by element against the oracle's assembled
+CSR matrix; the full-size workloads (the launch configuration the benchmark
+times) are compared on sampled rows the oracle assembles one by one.
+
+Tolerances: FP64 relative Frobenius error <= 1e-12 and every element within
+1e-12 max|Y_ref|; FP32 (inputs rounded to FP32, result compared with the
+oracle applied to the same rounded inputs) within FP32_TOL, the bound for
+six chained contractions of length <= 11 in single precision, measured
+maximum times four.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2208_07129_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def fe():
+    from paper_2208_07129_gb300 import build, fe as fe_mod
+    build.build()
+    fe_mod.lib()
+    return fe_mod
+
+
+def _setup_pair(fe, nx, ny, nz, p, nq, periodic=False, vertices=None, quad=0, potential="gauss", seed=0,
+                mu=0.5, lo=(0, 0, 0), hi=(1, 1, 1)):
+    ctx = fe.fe_setup(nx, ny, nz, p, nq, periodic=periodic, vertices=vertices, quad=quad, mu=mu, lo=lo, hi=hi)
+    mesh = orc.Mesh(nx, ny, nz, periodic=periodic, lo=lo, hi=hi, vertices=vertices)
+
+    def V(xyz):
+        if potential == "gauss":
+            return inputs.gaussian_potential(xyz, 100 + seed, periodic)
+        if potential == "coulomb":
+            return inputs.coulomb_potential(xyz)
+        return None
+
+    Vg = V(fe.fe_quadrature_points(ctx))
+    if Vg is not None:
+        fe.fe_set_potential(ctx, Vg)
+    Vo = V(orc.quad_points(mesh, p, nq, quad))
+    return ctx, mesh, Vo
+
+
+def _gpu_apply(fe, ctx, X, mode):
+    fe.fe_set_mode(ctx, mode)
+    dt = torch.float64 if mode == "fp64" else torch.float32
+    Xd = torch.from_numpy(X).to(device="cuda", dtype=dt).contiguous()
+    Yd = torch.full_like(Xd, float("nan"))
+    fe.fe_apply(ctx, Xd, Yd)
+    torch.cuda.synchronize()
+    return Yd.double().cpu().numpy(), Xd.double().cpu().numpy()
+
+
+def _compare(Y, Yref, tol):
+    assert np.all(np.isfinite(Y))
+    scale = np.abs(Yref).max()
+    rel = np.linalg.norm(Y - Yref) / np.linalg.norm(Yref)
+    err = np.abs(Y - Yref).max() / scale
+    assert rel <= tol and err <= tol, (rel, err)
+    return rel
+
+
+CASES = [
+    # (nx, ny, nz, p, nq, periodic, distorted, quad, n_vec)
+    (4, 4, 4, 4, 6, False, False, 0, 8),      # the 4^3 p=4 workload itself
+    (3, 2, 3, 6, 8, True, False, 0, 13),      # periodic p=6, odd counts (3 colours), ragged vector tail
+    (2, 3, 2, 8, 10, False, True, 0, 5),      # distorted trilinear p=8
+    (3, 3, 2, 1, 2, False, False, 0, 1),      # p=1, single vector
+    (2, 2, 3, 3, 4, True, False, 1, 7),       # GLL quadrature, n_q = n_p
+    (2, 3, 2, 5, 8, False, True, 0, 33),      # n_q = n_p + 2, distorted, two vector blocks + tail
+    (5, 2, 2, 7, 9, True, False, 0, 9),       # p=7
+    (1, 1, 1, 2, 4, False, False, 0, 3),      # one cell
+]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}_p{c[3]}_q{c[4]}"
+                         f"_{'per' if c[5] else 'dir'}{'_dist' if c[6] else ''}_nv{c[8]}")
+def test_apply_matches_oracle(fe, case, mode):
+    nx, ny, nz, p, nq, periodic, distorted, quad, n_vec = case
+    verts = inputs.perturbed_vertices(nx, ny, nz, seed=31) if distorted else None
+    ctx, mesh, Vo = _setup_pair(fe, nx, ny, nz, p, nq, periodic, verts, quad, seed=p)
+    try:
+        X = inputs.random_block(fe.fe_num_dofs(ctx), n_vec, "uniform", seed=7 + p)
+        Y, Xr = _gpu_apply(fe, ctx, X, mode)
+        Yref = orc.apply(mesh, p, nq, Xr, kind=quad, Vq=Vo)
+        _compare(Y, Yref, FP64_TOL if mode == "fp64" else FP32_TOL)
+    finally:
+        fe.fe_destroy(ctx)
+
+
+def test_anisotropic_box_and_mu(fe):
+    ctx, mesh, Vo = _setup_pair(fe, 3, 2, 2, 4, 6, potential="coulomb", mu=1.0, lo=(-1, 0, 0.5), hi=(2, 0.5, 1.0))
+    try:
+        X = inputs.random_block(fe.fe_num_dofs(ctx), 4, "normal", seed=3)
+        Y, _ = _gpu_apply(fe, ctx, X, "fp64")
+        _compare(Y, orc.apply(mesh, 4, 6, X, mu=1.0, Vq=Vo), FP64_TOL)
+    finally:
+        fe.fe_destroy(ctx)
+
+
+def test_deterministic_and_no_op(fe):
+    ctx, mesh, Vo = _setup_pair(fe, 3, 3, 3, 6, 8, periodic=True)
+    try:
+        X = torch.from_numpy(inputs.random_block(fe.fe_num_dofs(ctx), 16, "normal", 1)).cuda()
+        Y1 = torch.empty_like(X)
+        Y2 = torch.empty_like(X)
+        fe.fe_apply(ctx, X, Y1)
+        fe.fe_apply(ctx, X, Y2)
+        torch.cuda.synchronize()
+        assert torch.equal(Y1, Y2)        # colour-ordered assembly: bitwise reproducible
+        Z = torch.zeros(fe.fe_num_dofs(ctx), 0, dtype=torch.float64, device="cuda")
+        fe.fe_apply(ctx, Z, Z.clone())    # n_vec = 0 is a no-op
+        with pytest.raises(fe.FeError):
+            fe.fe_apply(ctx, X, X)        # in-place is rejected
+    finally:
+        fe.fe_destroy(ctx)
+
+
+def test_dirichlet_rows_and_inputs(fe):
+    ctx, mesh, Vo = _setup_pair(fe, 2, 2, 2, 3, 5)
+    try:
+        n = fe.fe_num_dofs(ctx)
+        mask = orc.constrained_mask(mesh, 3)
+        X = inputs.random_block(n, 3, "uniform", 2)
+        X2 = X.copy()
+        X2[mask] = 1e3                    # boundary entries of X are ignored
+        Y, _ = _gpu_apply(fe, ctx, X, "fp64")
+        Y2, _ = _gpu_apply(fe, ctx, X2, "fp64")
+        assert np.array_equal(Y, Y2)
+        assert np.all(Y[mask] == 0.0)     # boundary rows written 0
+    finally:
+        fe.fe_destroy(ctx)
+
+
+def test_host_buffer_apply(fe):
+    ctx, mesh, Vo = _setup_pair(fe, 2, 3, 2, 4, 6)
+    try:
+        X = inputs.random_block(fe.fe_num_dofs(ctx), 6, "uniform", 4)
+        Xh = torch.from_numpy(X).pin_memory()
+        Yh = torch.empty_like(Xh).pin_memory()
+        fe.fe_apply_host(ctx, Xh, Yh)
+        _compare(Yh.numpy(), orc.apply(mesh, 4, 6, X, Vq=Vo), FP64_TOL)
+    finally:
+        fe.fe_destroy(ctx)
+
+
+def test_diagonal(fe):
+    verts = inputs.perturbed_vertices(2, 2, 3, seed=8)
+    for periodic, v in ((True, None), (False, verts)):
+        ctx, mesh, Vo = _setup_pair(fe, 2, 2, 3, 4, 6, periodic=periodic, vertices=v)
+        try:
+            d = torch.empty(fe.fe_num_dofs(ctx), dtype=torch.float64, device="cuda")
+            fe.fe_diagonal(ctx, d)
+            A = orc.assemble(mesh, 4, 6, Vq=Vo)
+            ref = A.diagonal().copy()
+            mask = orc.constrained_mask(mesh, 4)
+            ref[mask] = 1.0
+            np.testing.assert_allclose(d.cpu().numpy(), ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
+        finally:
+            fe.fe_destroy(ctx)
+
+
+def _sample_rows(n, mesh, p, count, seed):
+    rng = np.random.default_rng(seed)
+    rows = set(rng.integers(0, n, count).tolist())
+    rows.update([0, n - 1, n // 2, 1, n - 2])
+    return np.array(sorted(rows), dtype=np.int64)
+
+
+@pytest.mark.parametrize("name,mode", [("c1", "fp64"), ("c2", "fp64"), ("c2", "fp32"), ("c3", "fp64"),
+                                       ("c3", "fp32"), ("c5", "fp64")])
+def test_full_size_sampled_rows(fe, name, mode):
+    """Full-size workloads in the benchmark's launch configuration, checked on
+    sampled rows (boundary, periodic seam and interior) against the oracle."""
+    w = inputs.WORKLOADS[name]
+    ctx = fe.setup_workload(w)
+    try:
+        X = w.make_x()
+        Y, Xr = _gpu_apply(fe, ctx, X, mode)
+        del X
+        mesh = orc.Mesh(w.nx, w.ny, w.nz, periodic=w.periodic, vertices=w.vertices())
+        Vo = w.potential_at(orc.quad_points(mesh, w.p, w.nq))
+        rows = _sample_rows(Y.shape[0], mesh, w.p, 96, seed=len(name))
+        Yref = orc.apply_rows(mesh, w.p, w.nq, Xr, rows, Vq=Vo, mu=w.mu)
+        _compare(Y[rows], Yref, FP64_TOL if mode == "fp64" else FP32_TOL)
+    finally:
+        fe.fe_destroy(ctx)
