@@ -128,6 +128,43 @@ fe_status fe_apply_host(fe_ctx* ctx, const void* X_host, void* Y_host, int n_vec
  * same tables: A_II = sum over cells containing I of A^(e)_ii. */
 fe_status fe_diagonal(fe_ctx* ctx, double* diag, void* stream);
 
+/* Preconditioners of fe_solve. */
+typedef enum { FE_PRECOND_NONE = 0, FE_PRECOND_JACOBI = 1, FE_PRECOND_LEARNED = 2 } fe_precond;
+
+typedef struct {
+  int iterations;          /* CG iterations (all inner iterations under refinement) */
+  int outer_iterations;    /* refinement steps (0 when inner_mode == FE_FP64) */
+  int fp64_applies;        /* applications of the FP64 operator */
+  int converged_columns;   /* columns with FP64 relative residual <= rtol */
+  double max_rel_residual; /* max_j ||b_j - A x_j|| / ||b_j||, FP64 operator */
+  double seconds;          /* device time of the whole solve (CUDA events) */
+} fe_solve_info;
+
+/* Solve A X = B for n_vec right-hand sides by block preconditioned conjugate
+ * gradients: one CG recurrence per column, all columns advanced together
+ * (the block Krylov setting the paper names for many right-hand sides; the
+ * operator is the matrix-free product of fe_apply).  B, X: device FP64,
+ * num_dofs x n_vec, DoF-major; X holds the initial guess on entry and the
+ * solution on return.  For a Dirichlet box B's boundary rows should be 0 and
+ * X's boundary rows stay 0.
+ *   inner_mode == FE_FP64: PCG in FP64.
+ *   otherwise: FP64 iterative refinement -- r = B - A X with the FP64
+ *   operator, an inner PCG in inner_mode (FP32 data; FE_FP32/TF32/BF16
+ *   operator) on r / ||r|| to relative tolerance 1e-4, X += ||r|| D -- until
+ *   every column reaches rtol.
+ * precond: FE_PRECOND_JACOBI (diag(A)^-1 from fe_diagonal), FE_PRECOND_NONE,
+ * or FE_PRECOND_LEARNED (the trained cell-patch network, see fe_learn.h;
+ * flexible CG, with FE_EINVAL when no network is loaded).
+ * Stops after max_it iterations.  Every final residual is measured with the
+ * FP64 operator; returns FE_ENOTCONV (with X and info filled) if a column
+ * misses rtol, FE_EBREAKDOWN if p^T A p <= 0 on an active column.
+ * info (host, optional) and rel_res (host, optional, n_vec doubles: the final
+ * FP64 relative residual of each column) are written on return.  Workspace
+ * (device) is allocated on first use and kept in the context.  Synchronous
+ * with respect to the host. */
+fe_status fe_solve(fe_ctx* ctx, const double* B, double* X, int n_vec, double rtol, int max_it, int precond,
+                   int inner_mode, fe_solve_info* info, double* rel_res, void* stream);
+
 /* Status word written by asynchronous device work (non-finite values met,
  * bounded waits that gave up); reading it synchronises the context's work and
  * clears it. */

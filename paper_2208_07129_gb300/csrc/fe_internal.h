@@ -49,6 +49,25 @@ struct ColorSet {
   std::vector<int> offset;  // n_colors + 1
 };
 
+// Workspace of the block-PCG solver, grown on demand and kept in the context.
+struct SolveWs {
+  double* v64[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t cap64[4] = {0, 0, 0, 0};
+  float* v32[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t cap32[6] = {0, 0, 0, 0, 0, 0};
+  double* colbuf = nullptr;  // per-column scalars
+  size_t cap_col = 0;
+  double* partial = nullptr; // per-CTA column partial sums
+  size_t cap_partial = 0;
+  int* active = nullptr;     // per-column "not yet converged" flags
+  size_t cap_active = 0;
+  double* diag = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+};
+
+struct LearnedPrecond;
+
 struct KernelLaunch {
   const int* cells;   // cell ids of this colour (device)
   int n_cells;
@@ -86,6 +105,9 @@ struct fe_ctx {
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
   fe_mode mode = FE_FP64;
+  fe_mode inner_mode = FE_FP32;   // arithmetic of the inner solve (refinement)
+  fe::SolveWs ws;
+  fe::LearnedPrecond* learned = nullptr;
   // launch shape per mode (vectors per CTA, lines per CTA)
   int vb64 = 8, nty64 = 16, vb32 = 32, nty32 = 8;
 };
@@ -95,4 +117,10 @@ namespace fe {
 cudaError_t apply_cc_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s);
 cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);
 cudaError_t diagonal_f64(const fe_ctx* c, double* diag, cudaStream_t s);
+// Solver workspace and the learned preconditioner (fe_solve.cu / fe_learn.cu).
+cudaError_t solver_workspace(fe_ctx* c, int nv);
+void free_solver_workspace(fe_ctx* c);
+bool learned_ready(const fe_ctx* c, int nv);
+fe_status learned_precond_apply(fe_ctx* c, const void* r, void* z, int nv, bool fp64, cudaStream_t s);
+void free_learned(fe_ctx* c);
 }  // namespace fe

@@ -315,6 +315,8 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->d_cells); cudaFree(c->d_cellG64); cudaFree(c->d_ptG64); cudaFree(c->d_ptC64);
   cudaFree(c->d_cellG32); cudaFree(c->d_ptG32); cudaFree(c->d_ptC32); cudaFree(c->d_detJ);
   cudaFree(c->d_status); cudaFree(c->d_stage);
+  free_solver_workspace(c);
+  free_learned(c);
   delete c;
 }
 

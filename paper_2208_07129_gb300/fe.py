@@ -36,6 +36,16 @@ class fe_mesh_desc(ctypes.Structure):
                 ("bc", ctypes.c_int), ("vertex_xyz", ctypes.POINTER(ctypes.c_double))]
 
 
+class fe_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("fp64_applies", ctypes.c_int),
+                ("converged_columns", ctypes.c_int), ("max_rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+FE_PRECOND_NONE, FE_PRECOND_JACOBI, FE_PRECOND_LEARNED = 0, 1, 2
+PRECONDS = {"none": FE_PRECOND_NONE, "jacobi": FE_PRECOND_JACOBI, "learned": FE_PRECOND_LEARNED}
+
+
 class fe_quad_desc(ctypes.Structure):
     _fields_ = [("n_q", ctypes.c_int), ("kind", ctypes.c_int)]
 
@@ -68,6 +78,8 @@ def lib() -> ctypes.CDLL:
         "fe_apply_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
         "fe_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
         "fe_last_device_status": (ctypes.c_int, [_VP]),
+        "fe_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.POINTER(fe_solve_info), _DP, _VP]),
         "fe_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -192,6 +204,30 @@ def fe_diagonal(ctx: int, diag, stream=None) -> None:
     if not diag.is_cuda or diag.dtype != torch.float64 or diag.numel() != fe_num_dofs(ctx):
         raise ValueError("diag must be a CUDA float64 tensor with num_dofs entries")
     _check(lib().fe_diagonal(ctx, diag.data_ptr(), _stream_ptr(stream)), "fe_diagonal")
+
+
+def fe_solve(ctx: int, B, X, rtol: float = 1e-8, max_it: int = 10000, precond="jacobi", inner_mode="fp64",
+             stream=None) -> dict:
+    """Block PCG for A X = B (FP64 torch tensors on the device; X = initial
+    guess in, solution out).  Returns the solve info with the per-column FP64
+    relative residuals; raises FeError unless the status is FE_OK or
+    FE_ENOTCONV (reported in the result)."""
+    import torch
+    for t, nm in ((B, "B"), (X, "X")):
+        if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.shape[0] != fe_num_dofs(ctx):
+            raise ValueError(f"{nm}: need a contiguous CUDA float64 tensor of shape (num_dofs, n_vec)")
+    n_vec = B.shape[1]
+    info = fe_solve_info()
+    rel = np.zeros(n_vec)
+    pc = PRECONDS[precond] if isinstance(precond, str) else int(precond)
+    im = MODES[inner_mode] if isinstance(inner_mode, str) else int(inner_mode)
+    st = lib().fe_solve(ctx, B.data_ptr(), X.data_ptr(), n_vec, rtol, max_it, pc, im, ctypes.byref(info),
+                        rel.ctypes.data_as(_DP), _stream_ptr(stream))
+    if st not in (FE_OK, FE_ENOTCONV):
+        raise FeError(st, "fe_solve")
+    return {"status": st, "iterations": info.iterations, "outer_iterations": info.outer_iterations,
+            "fp64_applies": info.fp64_applies, "converged_columns": info.converged_columns,
+            "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "rel_res": rel}
 
 
 def fe_last_device_status(ctx: int) -> int:

@@ -139,6 +139,9 @@ WORKLOADS = {
                    "normal", 2, "gauss", v_seed=12),
     "c3": Workload("perturbed 16^3 trilinear, p=8, n_q=10, Dirichlet-0, n_vec=256", 16, 16, 16, False, 8, 10, 256,
                    "uniform", 3, "gauss", v_seed=23, perturb_seed=13),
+    # a smaller case of the same kernel for hardware-counter captures (inputs still above L2)
+    "c2s": Workload("periodic box 12^3, p=6, n_q=8, n_vec=64", 12, 12, 12, True, 6, 8, 64,
+                    "normal", 2, "gauss", v_seed=12),
     "c5": Workload("24^3 unit cube, p=6, n_q=8, Dirichlet-0, 128 right-hand sides", 24, 24, 24, False, 6, 8, 128,
                    "normal", 5, "gauss", v_seed=15, v_amp=0.125, v_shift=1.0),
 }
