@@ -241,6 +241,43 @@ def time_mode(fe, torch, ctx, w, mode, steps, warmup, world):
     return ms, per, X, Y
 
 
+def solve_bench(fe, torch, sub_cols: int = 16):
+    """Time to relative residual 1e-8 (FP64 operator as judge) for the block
+    PCG solve of the 24^3, p=6, 128-column problem: mixed precision (FP32 inner
+    PCG with Jacobi, FP64 refinement) run to the end, and FP64 Jacobi-PCG
+    extrapolated from a full solve of `sub_cols` columns (its iteration count)
+    and the measured time per iteration at 128 columns."""
+    w = inputs.WORKLOADS["c5"]
+    ctx = fe.setup_workload(w)
+    out = {"workload": w.name, "rtol": 1e-8}
+    try:
+        Bd = torch.from_numpy(w.make_rhs()).cuda()
+        X = torch.zeros_like(Bd)
+        r = fe.fe_solve(ctx, Bd, X, rtol=1e-8, max_it=50000, precond="jacobi", inner_mode="fp32")
+        r.pop("rel_res")
+        out["mixed_fp32_jacobi"] = r
+        # FP64 Jacobi-PCG: iteration count from a full solve on the first sub_cols columns
+        Bs = Bd[:, :sub_cols].contiguous()
+        Xs = torch.zeros_like(Bs)
+        rs = fe.fe_solve(ctx, Bs, Xs, rtol=1e-8, max_it=50000, precond="jacobi", inner_mode="fp64")
+        rs.pop("rel_res")
+        # time per iteration at full width: difference of two capped solves
+        t = {}
+        for k in (2, 5):
+            X.zero_()
+            t[k] = fe.fe_solve(ctx, Bd, X, rtol=1e-8, max_it=k, precond="jacobi", inner_mode="fp64")["seconds"]
+        t_it = (t[5] - t[2]) / 3.0
+        out["fp64_jacobi"] = {"iterations_at_%d_columns" % sub_cols: rs["iterations"],
+                              "max_rel_residual_at_%d_columns" % sub_cols: rs["max_rel_residual"],
+                              "seconds_per_iteration_128_columns": t_it,
+                              "seconds_extrapolated": rs["iterations"] * t_it + (t[2] - 2 * t_it),
+                              "extrapolated": True}
+        out["speedup_mixed_vs_fp64"] = out["fp64_jacobi"]["seconds_extrapolated"] / r["seconds"]
+    finally:
+        fe.fe_destroy(ctx)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,6 +287,7 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--modes", default="fp64,fp32")
+    ap.add_argument("--no-solve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -357,6 +395,8 @@ def main():
         "gpu_launches": n_colors * args.steps,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_solve:
+        out["pcg"] = solve_bench(fe, torch)
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

@@ -150,8 +150,9 @@ typedef struct {
  *   inner_mode == FE_FP64: PCG in FP64.
  *   otherwise: FP64 iterative refinement -- r = B - A X with the FP64
  *   operator, an inner PCG in inner_mode (FP32 data; FE_FP32/TF32/BF16
- *   operator) on r / ||r|| to relative tolerance 1e-4, X += ||r|| D -- until
- *   every column reaches rtol.
+ *   operator) on r / ||r|| to the relative reduction still needed
+ *   (rtol ||b|| / (2 ||r||), at least 2e-6), X += ||r|| D -- until every
+ *   column reaches rtol.
  * precond: FE_PRECOND_JACOBI (diag(A)^-1 from fe_diagonal), FE_PRECOND_NONE,
  * or FE_PRECOND_LEARNED (the trained cell-patch network, see fe_learn.h;
  * flexible CG, with FE_EINVAL when no network is loaded).

@@ -1,13 +1,24 @@
-// FP32 CUDA-core instantiations of the fused cell kernel.
+// FP32 CUDA-core instantiations: the register-plane kernel for n_q <= 8 and
+// more than 16 vectors, the line kernel otherwise.
 #include "fe_dispatch.cuh"
+#include "fe_plane_kernel.cuh"
 
 namespace fe {
 
+namespace {
+template <int NP, int NQ, bool GEN>
+cudaError_t pick(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s) {
+  if constexpr (NQ <= 8) {
+    if (c->fp32_variant != 1 && (c->fp32_variant == 2 || n_vec > 16)) return launch_plane<NP, NQ, GEN>(c, X, Y, n_vec, s);
+  }
+  return launch_apply<float, NP, NQ, GEN>(c, X, Y, n_vec, s, c->vb32, c->nty32);
+}
+}  // namespace
+
 cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s) {
-#define FE_CASE(P, NQ)                                                                        \
-  if (c->p == P && c->nq == NQ)                                                               \
-    return c->general ? launch_apply<float, P + 1, NQ, true>(c, X, Y, n_vec, s, c->vb32, c->nty32) \
-                      : launch_apply<float, P + 1, NQ, false>(c, X, Y, n_vec, s, c->vb32, c->nty32);
+#define FE_CASE(P, NQ) \
+  if (c->p == P && c->nq == NQ) \
+    return c->general ? pick<P + 1, NQ, true>(c, X, Y, n_vec, s) : pick<P + 1, NQ, false>(c, X, Y, n_vec, s);
   FE_FOR_EACH_P_NQ(FE_CASE)
 #undef FE_CASE
   return cudaErrorInvalidValue;

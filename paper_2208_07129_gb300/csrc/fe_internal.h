@@ -110,6 +110,7 @@ struct fe_ctx {
   fe::LearnedPrecond* learned = nullptr;
   // launch shape per mode (vectors per CTA, lines per CTA)
   int vb64 = 8, nty64 = 16, vb32 = 32, nty32 = 8;
+  int fp32_variant = 0;   // 0: automatic, 1: line kernel, 2: register-plane kernel
 };
 
 namespace fe {

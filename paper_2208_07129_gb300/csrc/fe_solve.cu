@@ -361,9 +361,10 @@ extern "C" fe_status fe_solve(fe_ctx* c, const double* B, double* X, int nv, dou
     inf.iterations = its;
     fp64_applies = its + 1;
   } else {
-    // FP64 iterative refinement: r = b - A64 x; solve A32 d = r / ||r|| to a
-    // loose relative tolerance in the inner precision; x += ||r|| d.
-    const double inner_rtol = 1e-4;
+    // FP64 iterative refinement: r = b - A64 x; solve A32 d = r / ||r|| in the
+    // inner precision to the reduction still needed (rtol ||b|| / ||r||), but
+    // no further than FP32 can resolve (kInnerFloor); x += ||r|| d.
+    const double kInnerFloor = 2e-6;
     int total = 0, outer = 0;
     double* scale = w.colbuf + 9 * nv;
     double* unscale = w.colbuf + 10 * nv;
@@ -380,7 +381,7 @@ extern "C" fe_status fe_solve(fe_ctx* c, const double* B, double* X, int nv, dou
         const bool act = rel[j] > rtol && rn > 0;
         sc[j] = act ? 1.0 / rn : 0.0;   // converged columns get a zero right-hand side
         us[j] = act ? rn : 0.0;
-        tol[j] = act ? inner_rtol : 0.0;
+        tol[j] = act ? std::fmax(0.5 * rtol / rel[j], kInnerFloor) : 0.0;
       }
       cudaMemcpyAsync(scale, sc.data(), nv * sizeof(double), cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(unscale, us.data(), nv * sizeof(double), cudaMemcpyHostToDevice, s);

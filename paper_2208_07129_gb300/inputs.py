@@ -81,6 +81,21 @@ class Workload:
             v = (np.zeros(xyz.shape[:-1]) if v is None else v) + self.v_shift
         return v
 
+    def boundary_mask(self) -> np.ndarray:
+        """True on the Dirichlet boundary nodes (all False for a periodic box)."""
+        if self.periodic:
+            return np.zeros(self.num_dofs, dtype=bool)
+        N = [self.nx * self.p + 1, self.ny * self.p + 1, self.nz * self.p + 1]
+        g = np.arange(self.num_dofs)
+        gx, gy, gz = g % N[0], (g // N[0]) % N[1], g // (N[0] * N[1])
+        return (gx == 0) | (gy == 0) | (gz == 0) | (gx == N[0] - 1) | (gy == N[1] - 1) | (gz == N[2] - 1)
+
+    def make_rhs(self, n_vec: Optional[int] = None) -> np.ndarray:
+        """Right-hand sides: the seeded block with its Dirichlet rows set to 0."""
+        B = self.make_x(n_vec)
+        B[self.boundary_mask()] = 0.0
+        return B
+
     def make_x(self, n_vec: Optional[int] = None, seed: Optional[int] = None) -> np.ndarray:
         return random_block(self.num_dofs, self.n_vec if n_vec is None else n_vec,
                             self.x_dist, self.x_seed if seed is None else seed)
