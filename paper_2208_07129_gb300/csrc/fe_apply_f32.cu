@@ -1,5 +1,5 @@
-// FP32 CUDA-core instantiations: the register-plane kernel for n_q <= 8 and
-// more than 16 vectors, the line kernel otherwise.
+// FP32 CUDA-core instantiations: the line kernel, or the register-plane
+// kernel (n_q <= 8) when selected with fe_set_tile.
 #include "fe_dispatch.cuh"
 #include "fe_plane_kernel.cuh"
 
@@ -9,7 +9,7 @@ namespace {
 template <int NP, int NQ, bool GEN>
 cudaError_t pick(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s) {
   if constexpr (NQ <= 8) {
-    if (c->fp32_variant != 1 && (c->fp32_variant == 2 || n_vec > 16)) return launch_plane<NP, NQ, GEN>(c, X, Y, n_vec, s);
+    if (c->fp32_variant == 2) return launch_plane<NP, NQ, GEN>(c, X, Y, n_vec, s);
   }
   return launch_apply<float, NP, NQ, GEN>(c, X, Y, n_vec, s, c->vb32, c->nty32);
 }

@@ -109,8 +109,8 @@ struct fe_ctx {
   fe::SolveWs ws;
   fe::LearnedPrecond* learned = nullptr;
   // launch shape per mode (vectors per CTA, lines per CTA)
-  int vb64 = 8, nty64 = 16, vb32 = 32, nty32 = 8;
-  int fp32_variant = 0;   // 0: automatic, 1: line kernel, 2: register-plane kernel
+  int vb64 = 8, nty64 = 16, vb32 = 8, nty32 = 32;
+  int fp32_variant = 0;   // 0 / 1: line kernel, 2: register-plane kernel
 };
 
 namespace fe {
@@ -118,6 +118,7 @@ namespace fe {
 cudaError_t apply_cc_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s);
 cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);
 cudaError_t diagonal_f64(const fe_ctx* c, double* diag, cudaStream_t s);
+cudaError_t apply_mma_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s, bool bf16);
 // Solver workspace and the learned preconditioner (fe_solve.cu / fe_learn.cu).
 cudaError_t solver_workspace(fe_ctx* c, int nv);
 void free_solver_workspace(fe_ctx* c);

@@ -119,15 +119,17 @@ __global__ void cg_alpha_kernel(const double* rz, const double* pq, const int* a
   alpha[c] = a;
 }
 
-// beta = rz_new / rz_old (Fletcher-Reeves) or (rz_new - rz_mid) / rz_old
-// (Polak-Ribiere, flexible CG), then rz_old = rz_new.
-__global__ void cg_beta_kernel(const double* rz_new, const double* rz_mid, double* rz_old, const int* active,
-                               double* beta, int nv, int flexible) {
+// beta = rz_new / rz_old (standard PCG) or, for a variable preconditioner,
+// beta = -(z_new . A p) / (p . A p) (flexible CG, Notay 2000); then rz_old = rz_new.
+__global__ void cg_beta_kernel(const double* rz_new, const double* zq, const double* pq, double* rz_old,
+                               const int* active, double* beta, int nv, int flexible) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nv) return;
   double b = 0.0;
-  if (active[c] && rz_old[c] != 0.0) b = (flexible ? rz_new[c] - rz_mid[c] : rz_new[c]) / rz_old[c];
-  if (flexible && b < 0.0) b = 0.0;
+  if (active[c]) {
+    if (flexible) b = pq[c] > 0.0 ? -zq[c] / pq[c] : 0.0;
+    else if (rz_old[c] != 0.0) b = rz_new[c] / rz_old[c];
+  }
   beta[c] = b;
   rz_old[c] = rz_new[c];
 }
@@ -215,9 +217,21 @@ static fe_status apply_mode(fe_ctx* c, const T* X, T* Y, int nv, cudaStream_t s)
 // One preconditioned CG solve in precision T for A x = b with x0 = x (in/out).
 // Stops when every column has ||r_j|| <= tol_j (recurrence residual) or after
 // max_it iterations.  Returns the iterations performed.
+using PcgHook = void (*)(void* user, int it, const void* x, const void* r, cudaStream_t s);
+
+// With the learned (nonlinear) preconditioner, columns whose r.z is not
+// positive fall back to the Jacobi direction (descent safeguard).
+template <typename T>
+__global__ void fcg_safeguard_kernel(const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ z,
+                                     const double* __restrict__ rz, size_t total, int nv) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    if (!(rz[i % nv] > 0.0)) z[i] = r[i] * dinv[i / nv];
+}
+
 template <typename T>
 fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int max_it, int precond, cudaStream_t s,
-              T* r, T* z, T* p, T* q, int* iters_out, int check_every) {
+              T* r, T* z, T* p, T* q, int* iters_out, int check_every, PcgHook hook = nullptr,
+              void* hook_user = nullptr) {
   SolveWs& w = c->ws;
   const size_t n = c->n_dofs, tot = n * (size_t)nv;
   double* rz = w.colbuf;
@@ -228,7 +242,8 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
   double* rr = w.colbuf + 5 * nv;
   double* rzmid = w.colbuf + 6 * nv;
   const T* dinv = nullptr;
-  if (precond == FE_PRECOND_JACOBI) dinv = (const T*)(sizeof(T) == 8 ? (const void*)w.dinv64 : (const void*)w.dinv32);
+  const T* dinv_all = (const T*)(sizeof(T) == 8 ? (const void*)w.dinv64 : (const void*)w.dinv32);
+  if (precond == FE_PRECOND_JACOBI) dinv = dinv_all;
   const bool learned = precond == FE_PRECOND_LEARNED;
   cudaError_t e;
   std::vector<double> rr_h(nv);
@@ -238,11 +253,16 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
   fe_status st = apply_mode<T>(c, x, r, nv, s);
   if (st != FE_OK) return st;
   residual_kernel<T><<<ew_grid(tot), 256, 0, s>>>(b, r, tot);
+  if (hook) hook(hook_user, 0, x, r, s);
   if (learned) st = learned_precond_apply(c, r, z, nv, sizeof(T) == 8, s);
   else precond_jacobi_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv, z, n, nv);
   if (st != FE_OK) return st;
-  if ((e = cudaMemcpyAsync(p, z, tot * sizeof(T), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return from_cuda(e);
   if ((e = col_dot<T>(r, z, n, nv, w.partial, rz, s)) != cudaSuccess) return from_cuda(e);
+  if (learned) {
+    fcg_safeguard_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv_all, z, rz, tot, nv);
+    if ((e = col_dot<T>(r, z, n, nv, w.partial, rz, s)) != cudaSuccess) return from_cuda(e);
+  }
+  if ((e = cudaMemcpyAsync(p, z, tot * sizeof(T), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return from_cuda(e);
   if ((e = col_dot<T>(r, r, n, nv, w.partial, rr, s)) != cudaSuccess) return from_cuda(e);
   cudaMemcpyAsync(rr_h.data(), rr, nv * sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -258,17 +278,22 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
     cg_alpha_kernel<<<(nv + 127) / 128, 128, 0, s>>>(rz, pq, w.active, alpha, nv, c->d_status);
     cg_update_kernel<T><<<ew_grid(tot), 256, 0, s>>>(x, r, p, q, alpha, tot, nv);
     if (learned) {
-      // flexible CG: beta = (r_new.z_new - r_new.z_old) / r_old.z_old
-      if ((e = col_dot<T>(r, z, n, nv, w.partial, rzmid, s)) != cudaSuccess) return from_cuda(e);
       st = learned_precond_apply(c, r, z, nv, sizeof(T) == 8, s);
       if (st != FE_OK) return st;
     } else {
       precond_jacobi_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv, z, n, nv);
     }
     if ((e = col_dot<T>(r, z, n, nv, w.partial, rznew, s)) != cudaSuccess) return from_cuda(e);
-    cg_beta_kernel<<<(nv + 127) / 128, 128, 0, s>>>(rznew, rzmid, rz, w.active, beta, nv, learned ? 1 : 0);
+    if (learned) {
+      fcg_safeguard_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv_all, z, rznew, tot, nv);
+      if ((e = col_dot<T>(r, z, n, nv, w.partial, rznew, s)) != cudaSuccess) return from_cuda(e);
+      // flexible CG (Notay): beta = -(z_new . A p) / (p . A p)
+      if ((e = col_dot<T>(z, q, n, nv, w.partial, rzmid, s)) != cudaSuccess) return from_cuda(e);
+    }
+    cg_beta_kernel<<<(nv + 127) / 128, 128, 0, s>>>(rznew, rzmid, pq, rz, w.active, beta, nv, learned ? 1 : 0);
     cg_direction_kernel<T><<<ew_grid(tot), 256, 0, s>>>(p, z, beta, tot, nv);
     ++it;
+    if (hook) hook(hook_user, it, x, r, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return from_cuda(e);
     if (it % check_every == 0 || it == max_it) {
       if ((e = col_dot<T>(r, r, n, nv, w.partial, rr, s)) != cudaSuccess) return from_cuda(e);
@@ -310,6 +335,17 @@ fe_status true_residual(fe_ctx* c, const double* B, const double* X, int nv, dou
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return from_cuda(e);
   for (int j = 0; j < nv; ++j) rel[j] = bnorm[j] > 0 ? std::sqrt(h[j]) / bnorm[j] : std::sqrt(h[j]);
   return FE_OK;
+}
+
+fe_status pcg_f32_hooked(fe_ctx* c, const float* b, float* x, int nv, const double* tol, int max_it, PcgHook hook,
+                         void* user, int* its, cudaStream_t s) {
+  SolveWs& w = c->ws;
+  const fe_mode saved = c->inner_mode;
+  c->inner_mode = FE_FP32;
+  fe_status st = pcg<float>(c, b, x, nv, tol, max_it, FE_PRECOND_JACOBI, s, w.v32[0], w.v32[1], w.v32[2], w.v32[5],
+                            its, 8, hook, user);
+  c->inner_mode = saved;
+  return st;
 }
 
 void free_solver_workspace(fe_ctx* c) {

@@ -46,6 +46,18 @@ FE_PRECOND_NONE, FE_PRECOND_JACOBI, FE_PRECOND_LEARNED = 0, 1, 2
 PRECONDS = {"none": FE_PRECOND_NONE, "jacobi": FE_PRECOND_JACOBI, "learned": FE_PRECOND_LEARNED}
 
 
+class fe_train_desc(ctypes.Structure):
+    _fields_ = [("n_rhs", ctypes.c_int), ("snapshots", ctypes.c_int), ("snapshot_every", ctypes.c_int),
+                ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("traj_rtol", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
+class fe_train_info(ctypes.Structure):
+    _fields_ = [("samples", ctypes.c_longlong), ("steps", ctypes.c_int), ("trajectory_iterations", ctypes.c_int),
+                ("loss_first_step", ctypes.c_float), ("loss_first_epoch", ctypes.c_float),
+                ("loss_last_epoch", ctypes.c_float), ("seconds", ctypes.c_double)]
+
+
 class fe_quad_desc(ctypes.Structure):
     _fields_ = [("n_q", ctypes.c_int), ("kind", ctypes.c_int)]
 
@@ -81,6 +93,16 @@ def lib() -> ctypes.CDLL:
         "fe_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.POINTER(fe_solve_info), _DP, _VP]),
         "fe_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+        "fe_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "fe_precond_init": (ctypes.c_int, [_VP, ctypes.c_ulonglong]),
+        "fe_precond_train": (ctypes.c_int, [_VP, ctypes.POINTER(fe_train_desc), ctypes.POINTER(fe_train_info), _VP]),
+        "fe_precond_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+        "fe_precond_set_weights": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+        "fe_precond_get_weights": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+        "fe_precond_input_size": (ctypes.c_int, [_VP]),
+        "fe_precond_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+        "fe_precond_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+        "fe_mlp_gradients": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -169,6 +191,11 @@ def fe_set_mode(ctx: int, mode) -> None:
     _check(lib().fe_set_mode(ctx, m), "fe_set_mode")
 
 
+def fe_set_tile(ctx: int, mode, vectors_per_cta: int, lines: int, variant: int = 0) -> None:
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(lib().fe_set_tile(ctx, m, vectors_per_cta, lines, variant), "fe_set_tile")
+
+
 def fe_get_mode(ctx: int) -> int:
     return int(lib().fe_get_mode(ctx))
 
@@ -228,6 +255,72 @@ def fe_solve(ctx: int, B, X, rtol: float = 1e-8, max_it: int = 10000, precond="j
     return {"status": st, "iterations": info.iterations, "outer_iterations": info.outer_iterations,
             "fp64_applies": info.fp64_applies, "converged_columns": info.converged_columns,
             "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "rel_res": rel}
+
+
+HIDDEN = 128
+
+
+def fe_precond_input_size(ctx: int) -> int:
+    return int(lib().fe_precond_input_size(ctx))
+
+
+def fe_precond_init(ctx: int, seed: int = 0) -> None:
+    _check(lib().fe_precond_init(ctx, seed), "fe_precond_init")
+
+
+def fe_precond_set_weights(ctx: int, W1, b1, W2, b2) -> None:
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (W1, b1, W2, b2)]
+    n3 = fe_precond_input_size(ctx)
+    if arrs[0].shape != (HIDDEN, n3) or arrs[1].shape != (HIDDEN,) or arrs[2].shape != (n3, HIDDEN) \
+            or arrs[3].shape != (n3,):
+        raise ValueError("weights must be W1 (128, n3), b1 (128,), W2 (n3, 128), b2 (n3,)")
+    _check(lib().fe_precond_set_weights(ctx, *[a.ctypes.data for a in arrs]), "fe_precond_set_weights")
+
+
+def fe_precond_get_weights(ctx: int):
+    n3 = fe_precond_input_size(ctx)
+    out = [np.zeros((HIDDEN, n3), np.float32), np.zeros(HIDDEN, np.float32), np.zeros((n3, HIDDEN), np.float32),
+           np.zeros(n3, np.float32)]
+    _check(lib().fe_precond_get_weights(ctx, *[a.ctypes.data for a in out]), "fe_precond_get_weights")
+    return out
+
+
+def fe_precond_train(ctx: int, n_rhs=8, snapshots=8, snapshot_every=25, epochs=4, batch=4096, lr=1e-3,
+                     traj_rtol=1e-6, seed=0, stream=None) -> dict:
+    d = fe_train_desc(n_rhs, snapshots, snapshot_every, epochs, batch, lr, traj_rtol, seed)
+    info = fe_train_info()
+    _check(lib().fe_precond_train(ctx, ctypes.byref(d), ctypes.byref(info), _stream_ptr(stream)), "fe_precond_train")
+    return {f: getattr(info, f) for f, _ in fe_train_info._fields_}
+
+
+def fe_precond_apply(ctx: int, R, Z, stream=None) -> None:
+    import torch
+    for t, nm in ((R, "R"), (Z, "Z")):
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.shape[0] != fe_num_dofs(ctx):
+            raise ValueError(f"{nm}: need a contiguous CUDA float32 tensor of shape (num_dofs, n_vec)")
+    _check(lib().fe_precond_apply(ctx, R.data_ptr(), Z.data_ptr(), R.shape[1], _stream_ptr(stream)),
+           "fe_precond_apply")
+
+
+def fe_precond_save(ctx: int, path: str) -> None:
+    _check(lib().fe_precond_save(ctx, path.encode()), "fe_precond_save")
+
+
+def fe_precond_load(ctx: int, path: str) -> None:
+    _check(lib().fe_precond_load(ctx, path.encode()), "fe_precond_load")
+
+
+def fe_mlp_gradients(ctx: int, U, T, stream=None):
+    """Loss and gradients of the training objective (device tensors in, torch tensors out)."""
+    import torch
+    n3 = fe_precond_input_size(ctx)
+    dev = U.device
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    g = [torch.zeros(HIDDEN, n3, device=dev), torch.zeros(HIDDEN, device=dev), torch.zeros(n3, HIDDEN, device=dev),
+         torch.zeros(n3, device=dev)]
+    _check(lib().fe_mlp_gradients(ctx, U.data_ptr(), T.data_ptr(), U.shape[0], loss.data_ptr(),
+                                  *[x.data_ptr() for x in g], _stream_ptr(stream)), "fe_mlp_gradients")
+    return loss, g
 
 
 def fe_last_device_status(ctx: int) -> int:

@@ -21,6 +21,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 FP32_TOL = 2e-6
+TOL = {"fp64": FP64_TOL, "fp32": FP32_TOL, "tf32": 5e-3, "bf16": 5e-2}
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +83,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32", "bf16"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}_p{c[3]}_q{c[4]}"
                          f"_{'per' if c[5] else 'dir'}{'_dist' if c[6] else ''}_nv{c[8]}")
 def test_apply_matches_oracle(fe, case, mode):
@@ -93,7 +94,8 @@ def test_apply_matches_oracle(fe, case, mode):
         X = inputs.random_block(fe.fe_num_dofs(ctx), n_vec, "uniform", seed=7 + p)
         Y, Xr = _gpu_apply(fe, ctx, X, mode)
         Yref = orc.apply(mesh, p, nq, Xr, kind=quad, Vq=Vo)
-        _compare(Y, Yref, FP64_TOL if mode == "fp64" else FP32_TOL)
+        rel = _compare(Y, Yref, TOL[mode])
+        print(f"{mode} rel {rel:.3e}")
     finally:
         fe.fe_destroy(ctx)
 
@@ -178,7 +180,8 @@ def _sample_rows(n, mesh, p, count, seed):
 
 
 @pytest.mark.parametrize("name,mode", [("c1", "fp64"), ("c2", "fp64"), ("c2", "fp32"), ("c3", "fp64"),
-                                       ("c3", "fp32"), ("c5", "fp64")])
+                                       ("c3", "fp32"), ("c3", "tf32"), ("c3", "bf16"), ("c2", "tf32"),
+                                       ("c5", "fp64")])
 def test_full_size_sampled_rows(fe, name, mode):
     """Full-size workloads in the benchmark's launch configuration, checked on
     sampled rows (boundary, periodic seam and interior) against the oracle."""
@@ -192,6 +195,7 @@ def test_full_size_sampled_rows(fe, name, mode):
         Vo = w.potential_at(orc.quad_points(mesh, w.p, w.nq))
         rows = _sample_rows(Y.shape[0], mesh, w.p, 96, seed=len(name))
         Yref = orc.apply_rows(mesh, w.p, w.nq, Xr, rows, Vq=Vo, mu=w.mu)
-        _compare(Y[rows], Yref, FP64_TOL if mode == "fp64" else FP32_TOL)
+        rel = _compare(Y[rows], Yref, TOL[mode])
+        print(f"{name} {mode} rel {rel:.3e}")
     finally:
         fe.fe_destroy(ctx)
