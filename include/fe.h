@@ -120,7 +120,7 @@ fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream)
 /* Launch shape of the CUDA-core cell kernels of one mode (the autotuner's
  * knob): vectors per CTA (power of two, 1..32; halved further when shared
  * memory does not hold it, and never above the padded n_vec), lines in flight
- * per CTA (1..32; CTAs are capped at 256 threads), and the variant
+ * per CTA (1..256; CTAs are capped at 256 threads), and the variant
  * (0 or 1: line kernel; 2: register-plane kernel, FE_FP32 with n_q <= 8 only).
  * FE_EUNSUPPORTED for the tensor-core modes, whose tile is fixed.  Applies to
  * later fe_apply calls. */

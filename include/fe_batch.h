@@ -1,0 +1,59 @@
+/*
+ * fe_batch.h -- many operators applied in one persistent launch (see fe.h).
+ *
+ * The paper evaluates all cells and all vector batches of one operator
+ * concurrently in a single kernel launch (Sec. 3.1.2, GPU batched strategy);
+ * this call extends that to a batch of independent operators of different
+ * size, degree and block width.  One persistent kernel takes work items
+ * (problem, cell colour, range of cells, vector block) from a queue ordered
+ * by colour phase; an item of colour k waits (bounded) until its problem's
+ * colour k-1 items are done, so assembly stays conflict-free and every Y is
+ * bitwise the one fe_apply produces.  The kernel and the reset of its queue
+ * are captured once in a CUDA graph; each fe_batch_apply replays it.
+ */
+#ifndef FE_BATCH_H_
+#define FE_BATCH_H_
+
+#include "fe.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe_batch fe_batch;
+
+typedef struct {
+  int problems;
+  int work_items;
+  int phases;           /* colour phases of the queue */
+  int grid;             /* persistent CTAs */
+  long long smem_bytes; /* dynamic shared memory per CTA */
+  float autotune_ms;    /* device time spent timing candidate tiles */
+  int device_status;    /* FE_ETIMEOUT if a bounded wait gave up during an apply, else 0 */
+} fe_batch_info;
+
+/* Plan a batch over n contexts (each a degree 3..8 operator with n_q = p + 2
+ * on affine cells; FE_EUNSUPPORTED otherwise) with fixed block widths
+ * n_vec[i] > 0 (host array), in mode FE_FP64 or FE_FP32.  With autotune != 0
+ * the vectors per work item of every (degree, block-width bucket) are chosen
+ * by timing the candidates on a 4^3 periodic proxy mesh; otherwise a fixed
+ * rule is used.  The contexts must outlive the batch.  Synchronous. */
+fe_status fe_batch_create(fe_ctx* const* ctxs, int n, const int* n_vec, fe_mode mode, int autotune, fe_batch** out);
+
+/* Y[i] = A_i X[i] for every problem: X, Y host arrays of n device pointers
+ * (dtype of the batch's mode, num_dofs_i x n_vec[i], X[i] != Y[i]).  Waits
+ * for earlier work on `stream`, uploads the pointer table and replays the
+ * graph on `stream` (asynchronous from there). */
+fe_status fe_batch_apply(fe_batch* b, const void* const* X, void* const* Y, void* stream);
+
+/* Plan statistics; vectors_per_cta / cells_per_item (optional, n entries)
+ * receive each problem's tile.  Synchronous. */
+fe_status fe_batch_stats(const fe_batch* b, fe_batch_info* info, int* vectors_per_cta, int* cells_per_item);
+
+void fe_batch_destroy(fe_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE_BATCH_H_ */

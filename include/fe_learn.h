@@ -24,6 +24,16 @@
 extern "C" {
 #endif
 
+/* Training objectives. */
+typedef enum {
+  /* mean over residual snapshots r (columns scaled to norm 1) of (A z(r) - r)^2:
+     the network learns to make A z close to r, i.e. z close to A^-1 r where A
+     acts strongly; the gradient runs through the operator itself */
+  FE_TRAIN_OPERATOR_RESIDUAL = 0,
+  /* patch regression onto the oscillatory part of the error (see below) */
+  FE_TRAIN_PATCH_ERROR = 1
+} fe_train_objective;
+
 typedef struct {
   int n_rhs;               /* right-hand sides ~ N(0,1) of the training trajectories */
   int snapshots;           /* (r_k, x_k) snapshots recorded per trajectory, k = 0, every, 2 every, ... */
@@ -33,6 +43,7 @@ typedef struct {
   float lr;                /* Adam learning rate */
   double traj_rtol;        /* relative residual of the trajectory solve that gives x* */
   unsigned long long seed; /* seeds the right-hand sides, the initial weights and the shuffling */
+  int objective;           /* fe_train_objective */
 } fe_train_desc;
 
 typedef struct {
@@ -49,11 +60,16 @@ typedef struct {
  * biases 0), seeded.  Synchronous. */
 fe_status fe_precond_init(fe_ctx* ctx, unsigned long long seed);
 
-/* Train on residual / error pairs generated by an FP32 Jacobi-PCG solve of
- * this operator: inputs R_e r_k / s_e, targets HF(R_e(x* - x_k - D^-1 r_k)) / s_e,
- * where HF subtracts the trilinear interpolant of the patch's eight corner
- * values (the smooth part no cell-local map can predict), mean squared error,
- * Adam.  Initialises the weights first when none are set.
+/* Train on the residual / error trajectory of an FP32 Jacobi-PCG solve of this
+ * operator (n_rhs random right-hand sides, snapshots (r_k, x_k) every
+ * snapshot_every iterations, x* = the converged solution), with Adam:
+ *  FE_TRAIN_OPERATOR_RESIDUAL: one snapshot r_k per step, loss
+ *    mean (A z(r_k) - r_k)^2 over all cells' patches at once (two FP32
+ *    operator applications per step: A z and the gradient A (A z - r));
+ *  FE_TRAIN_PATCH_ERROR: inputs R_e r_k / s_e, targets
+ *    HF(R_e(x* - x_k - D^-1 r_k)) / s_e, HF subtracting the trilinear
+ *    interpolant of the patch's eight corner values, mini-batches of `batch`
+ *    patches, mean squared error.  Initialises the weights first when none are set.
  * Device memory for the samples is allocated for the call and released.
  * info (host, optional) receives the statistics.  Synchronous. */
 fe_status fe_precond_train(fe_ctx* ctx, const fe_train_desc* desc, fe_train_info* info, void* stream);

@@ -1,0 +1,377 @@
+// Batched uneven workload: many operators (different meshes, degrees and
+// block widths) applied by ONE persistent kernel, launched from a CUDA graph.
+//
+// Work items are (problem, colour, range of cells of that colour, vector
+// block).  The queue is ordered by colour phase first (all problems' colour-0
+// items, then colour 1, ...), so an item of colour k > 0 of problem i only has
+// to wait until every colour k-1 item of problem i is done; those were taken
+// from the queue earlier by running CTAs, so the wait always ends (and it is
+// bounded besides: a CTA that gives up records FE_ETIMEOUT).  Within a colour
+// the cells share no node, so assembly stays conflict-free and the result is
+// bitwise the one of the per-problem launches (Sec. 3.1.2: all cells and
+// batches of vectors evaluated concurrently, here across problems too).
+//
+// Each problem gets its own tile (vectors per item x lines per CTA, 128
+// threads) from a small autotuner that times the candidate tiles on a proxy
+// mesh of the same degree and block width, and a cell-batch size (cells per
+// item) that keeps the queue several items deep per SM.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "fe_internal.h"
+#include "fe_cell_kernel.cuh"
+#include "fe_dispatch.cuh"
+#include "../../include/fe_batch.h"
+
+namespace fe {
+
+constexpr int kBatchThreads = 128;
+constexpr int kMaxColors = 27;
+
+template <typename T>
+struct BatchProblemDev {
+  MeshDev m;
+  Geom<T> geo;
+  int n_vec, vb, nty, kind, n_vb;
+  const int* cells;                                    // colour-sorted cell ids
+  T tab[kMaxNQ * (kMaxP + 1) + kMaxNQ * kMaxNQ];       // Tables<T, NP, NQ> image (N then D)
+};
+
+struct WorkItem {
+  int problem, color, cell_begin, cell_count, vb;
+};
+
+// kinds: p = 3..8 with n_q = p + 2 on affine cells
+constexpr int kind_of(int p) { return p - 3; }
+
+template <typename T, int NP, int NQ>
+__device__ __forceinline__ void run_item(const BatchProblemDev<T>& P, const WorkItem& w, const T* X, T* Y, T* smem,
+                                         const T* stab) {
+  const Tables<T, NP, NQ>& tab = *reinterpret_cast<const Tables<T, NP, NQ>*>(stab);
+  const int tid = threadIdx.x, vb = P.vb;
+  const int v = tid % vb, ty = tid / vb, nty = kBatchThreads / vb;
+  for (int c = 0; c < w.cell_count; ++c) {
+    const int e = P.cells[w.cell_begin + c];
+    cell_body<T, NP, NQ, false>(tab, P.m, P.geo, e, w.vb, vb, v, ty, nty, P.n_vec, X, Y, smem);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchProblemDev<T>* __restrict__ probs,
+                                                             const void* const* __restrict__ ptrs,
+                                                             const WorkItem* __restrict__ items, int n_items,
+                                                             int* next, int* done, const int* __restrict__ need,
+                                                             int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) T stab[kMaxNQ * (kMaxP + 1) + kMaxNQ * kMaxNQ];
+  __shared__ int s_item;
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const WorkItem w = items[it];
+    const BatchProblemDev<T>& P = probs[w.problem];
+    if (threadIdx.x == 0 && w.color > 0) {
+      const int idx = w.problem * kMaxColors + w.color - 1;
+      long long spins = 0;
+      while (atomicAdd(&done[idx], 0) < need[idx]) {
+        __nanosleep(128);
+        if (++spins > (1LL << 26)) {
+          atomicMax(status, (int)FE_ETIMEOUT);
+          break;
+        }
+      }
+      __threadfence();
+    }
+    for (int k = threadIdx.x; k < kMaxNQ * (kMaxP + 1) + kMaxNQ * kMaxNQ; k += blockDim.x) stab[k] = P.tab[k];
+    __syncthreads();
+    const T* X = static_cast<const T*>(ptrs[2 * w.problem]);
+    T* Y = static_cast<T*>(const_cast<void*>(ptrs[2 * w.problem + 1]));
+    switch (P.kind) {
+      case 0: run_item<T, 4, 5>(P, w, X, Y, smem, stab); break;
+      case 1: run_item<T, 5, 6>(P, w, X, Y, smem, stab); break;
+      case 2: run_item<T, 6, 7>(P, w, X, Y, smem, stab); break;
+      case 3: run_item<T, 7, 8>(P, w, X, Y, smem, stab); break;
+      case 4: run_item<T, 8, 9>(P, w, X, Y, smem, stab); break;
+      case 5: run_item<T, 9, 10>(P, w, X, Y, smem, stab); break;
+      default: break;
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&done[w.problem * kMaxColors + w.color], 1);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+struct fe_batch {
+  int n = 0;
+  fe_mode mode = FE_FP64;
+  std::vector<fe_ctx*> ctxs;
+  std::vector<int> n_vec, vb, cells_per_item;
+  void* d_probs = nullptr;
+  WorkItem* d_items = nullptr;
+  int n_items = 0, n_phases = 0;
+  int *d_next = nullptr, *d_done = nullptr, *d_need = nullptr, *d_status = nullptr;
+  const void** h_ptrs = nullptr;   // pinned host staging of the X / Y table
+  void** d_ptrs = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  float tune_ms = 0.f;
+};
+
+namespace {
+
+fe_status from_cuda(cudaError_t e) {
+  return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
+}
+
+template <typename T>
+size_t tile_smem(int nq, int vb) { return (size_t)3 * nq * nq * nq * vb * sizeof(T); }
+
+// Candidate vectors-per-CTA of the autotuner for one problem.
+std::vector<int> candidates(int nq, int n_vec, size_t elem) {
+  std::vector<int> out;
+  for (int vb : {2, 4, 8, 16, 32}) {
+    if ((size_t)3 * nq * nq * nq * vb * elem > 110 * 1024) continue;   // keep two CTAs per SM
+    if (vb > 1 && vb / 2 >= n_vec) continue;
+    out.push_back(vb);
+  }
+  if (out.empty()) out.push_back(2);
+  return out;
+}
+
+// Time one apply of a 4^3 periodic proxy with the problem's degree and block
+// width for every candidate tile; return the fastest vectors-per-CTA.
+int autotune(const fe_ctx* c, int n_vec, fe_mode mode, float* spent_ms) {
+  const size_t elem = mode == FE_FP64 ? 8 : 4;
+  std::vector<int> cand = candidates(c->nq, n_vec, elem);
+  if (cand.size() == 1) return cand[0];
+  fe_mesh_desc md{};
+  md.nx = md.ny = md.nz = 4;
+  md.hi[0] = md.hi[1] = md.hi[2] = 1.0;
+  md.bc = FE_BC_PERIODIC;
+  fe_quad_desc qd{c->nq, c->quad_kind};
+  fe_ctx* px = nullptr;
+  if (fe_setup(&md, c->p, &qd, c->mu, &px) != FE_OK) return cand[0];
+  fe_set_mode(px, mode);
+  const size_t bytes = px->n_dofs * (size_t)n_vec * elem;
+  void *X = nullptr, *Y = nullptr;
+  int best = cand[0];
+  if (cudaMalloc(&X, bytes) == cudaSuccess && cudaMalloc(&Y, bytes) == cudaSuccess) {
+    cudaMemset(X, 0, bytes);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best_ms = 1e30f;
+    for (int vb : cand) {
+      fe_set_tile(px, mode, vb, kBatchThreads / vb, 1);
+      fe_apply(px, X, Y, n_vec, nullptr);
+      cudaEventRecord(a);
+      for (int r = 0; r < 3; ++r) fe_apply(px, X, Y, n_vec, nullptr);
+      cudaEventRecord(b);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      *spent_ms += ms;
+      if (ms < best_ms) { best_ms = ms; best = vb; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  cudaFree(X);
+  cudaFree(Y);
+  fe_destroy(px);
+  cudaGetLastError();
+  return best;
+}
+
+template <typename T>
+fe_status build_batch(fe_batch* b, int autotune_on) {
+  const int n = b->n;
+  std::vector<BatchProblemDev<T>> hp(n);
+  std::vector<int> need((size_t)n * kMaxColors, 0);
+  std::map<std::pair<int, int>, int> tuned;   // (p, n_vec bucket) -> vb
+  size_t smem = 0;
+  long long total_units = 0;
+  for (int i = 0; i < n; ++i) total_units += (long long)b->ctxs[i]->n_cells * ((b->n_vec[i] + 7) / 8);
+  for (int i = 0; i < n; ++i) {
+    fe_ctx* c = b->ctxs[i];
+    BatchProblemDev<T>& P = hp[i];
+    P.m = c->mdev;
+    if (b->mode == FE_FP64) P.geo = Geom<T>{(const T*)c->d_cellG64, (const T*)c->d_ptG64, (const T*)c->d_ptC64};
+    else P.geo = Geom<T>{(const T*)c->d_cellG32, (const T*)c->d_ptG32, (const T*)c->d_ptC32};
+    P.n_vec = b->n_vec[i];
+    P.kind = kind_of(c->p);
+    P.cells = c->d_cells;
+    const int bucket = (int)std::ceil(std::log2((double)std::max(1, P.n_vec)));
+    int vb;
+    auto key = std::make_pair(c->p, bucket);
+    if (!autotune_on) {
+      vb = candidates(c->nq, P.n_vec, sizeof(T)).back();
+      vb = std::min(vb, 8);
+    } else if (tuned.count(key)) {
+      vb = tuned[key];
+    } else {
+      vb = autotune(c, P.n_vec, b->mode, &b->tune_ms);
+      tuned[key] = vb;
+    }
+    P.vb = vb;
+    P.nty = kBatchThreads / vb;
+    P.n_vb = (P.n_vec + vb - 1) / vb;
+    b->vb[i] = vb;
+    std::memset(P.tab, 0, sizeof(P.tab));
+    for (int q = 0; q < c->nq; ++q) {
+      for (int k = 0; k < c->np; ++k) P.tab[q * c->np + k] = (T)c->Nf[q * c->np + k];
+      for (int k = 0; k < c->nq; ++k) P.tab[c->nq * c->np + q * c->nq + k] = (T)c->Df[q * c->nq + k];
+    }
+    smem = std::max(smem, tile_smem<T>(c->nq, vb));
+  }
+  // work items, phase-major
+  std::vector<WorkItem> items;
+  int phases = 0;
+  for (int k = 0; k < kMaxColors; ++k) {
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      fe_ctx* c = b->ctxs[i];
+      if (k >= c->colors.n_colors) continue;
+      any = true;
+      const int c0 = c->colors.offset[k], c1 = c->colors.offset[k + 1];
+      const BatchProblemDev<T>& P = hp[i];
+      // cells per item: keep >= ~8 items per SM over the whole batch
+      const long long per_color = (long long)(c1 - c0) * P.n_vb;
+      int cb = 1;
+      while (cb < 8 && per_color / (2 * cb) >= 64 && total_units / (2 * cb) > 152 * 32) cb *= 2;
+      b->cells_per_item[i] = cb;
+      for (int s = c0; s < c1; s += cb)
+        for (int v = 0; v < P.n_vb; ++v) {
+          items.push_back(WorkItem{i, k, s, std::min(cb, c1 - s), v});
+          need[(size_t)i * kMaxColors + k]++;
+        }
+    }
+    if (any) phases = k + 1;
+  }
+  b->n_items = (int)items.size();
+  b->n_phases = phases;
+  b->smem = smem;
+  cudaError_t e = cudaMalloc(&b->d_probs, n * sizeof(BatchProblemDev<T>));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_probs, hp.data(), n * sizeof(BatchProblemDev<T>), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_items, std::max<size_t>(1, items.size()) * sizeof(WorkItem));
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_need, need.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_done, need.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, 2 * n * sizeof(void*));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_ptrs, 2 * n * sizeof(void*));
+  if (e == cudaSuccess && smem > 48 * 1024)
+    e = cudaFuncSetAttribute(batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<T>, kBatchThreads, smem);
+  if (e != cudaSuccess) return from_cuda(e);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  b->grid = std::max(1, std::min(b->n_items, std::max(1, per_sm) * sms));
+  // graph: reset the queue and the colour counters, then the persistent kernel
+  e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(b->d_next, 0, sizeof(int), b->cap);
+    cudaMemsetAsync(b->d_done, 0, need.size() * sizeof(int), b->cap);
+    batch_kernel<T><<<b->grid, kBatchThreads, smem, b->cap>>>(
+        static_cast<const BatchProblemDev<T>*>(b->d_probs), const_cast<const void* const*>(b->d_ptrs), b->d_items,
+        b->n_items, b->d_next, b->d_done, b->d_need, b->d_status);
+    e = cudaStreamEndCapture(b->cap, &b->graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  return from_cuda(e);
+}
+
+}  // namespace
+
+extern "C" fe_status fe_batch_create(fe_ctx* const* ctxs, int n, const int* n_vec, fe_mode mode, int autotune_on,
+                                     fe_batch** out) {
+  if (!out) return FE_EINVAL;
+  *out = nullptr;
+  if (!ctxs || !n_vec || n <= 0) return FE_EINVAL;
+  if (mode != FE_FP64 && mode != FE_FP32) return FE_EUNSUPPORTED;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || n_vec[i] <= 0) return FE_EINVAL;
+    if (ctxs[i]->general || ctxs[i]->p < 3 || ctxs[i]->p > 8 || ctxs[i]->nq != ctxs[i]->p + 2) return FE_EUNSUPPORTED;
+  }
+  fe_batch* b = new fe_batch();
+  b->n = n;
+  b->mode = mode;
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->n_vec.assign(n_vec, n_vec + n);
+  b->vb.assign(n, 0);
+  b->cells_per_item.assign(n, 1);
+  fe_status st = mode == FE_FP64 ? build_batch<double>(b, autotune_on) : build_batch<float>(b, autotune_on);
+  if (st != FE_OK) {
+    fe_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return FE_OK;
+}
+
+extern "C" fe_status fe_batch_apply(fe_batch* b, const void* const* X, void* const* Y, void* stream) {
+  if (!b || !X || !Y) return FE_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < b->n; ++i) {
+    if (!X[i] || !Y[i] || X[i] == Y[i]) return FE_EINVAL;
+    b->h_ptrs[2 * i] = X[i];
+    b->h_ptrs[2 * i + 1] = Y[i];
+  }
+  // the table is read by the kernel of this launch; wait for the previous use of the staging buffer
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ptrs, b->h_ptrs, 2 * b->n * sizeof(void*), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+  return from_cuda(e);
+}
+
+extern "C" fe_status fe_batch_stats(const fe_batch* b, fe_batch_info* info, int* vectors_per_cta, int* cells_per_item) {
+  if (!b || !info) return FE_EINVAL;
+  info->problems = b->n;
+  info->work_items = b->n_items;
+  info->phases = b->n_phases;
+  info->grid = b->grid;
+  info->smem_bytes = (long long)b->smem;
+  info->autotune_ms = b->tune_ms;
+  for (int i = 0; i < b->n; ++i) {
+    if (vectors_per_cta) vectors_per_cta[i] = b->vb[i];
+    if (cells_per_item) cells_per_item[i] = b->cells_per_item[i];
+  }
+  int h = 0;
+  cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  info->device_status = h;
+  return FE_OK;
+}
+
+extern "C" void fe_batch_destroy(fe_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_probs); cudaFree(b->d_items); cudaFree(b->d_need); cudaFree(b->d_done); cudaFree(b->d_next);
+  cudaFree(b->d_status); cudaFree(b->d_ptrs);
+  if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
+  delete b;
+}

@@ -56,22 +56,18 @@ __device__ __forceinline__ bool on_boundary(int g, int N, int periodic) {
   return !periodic && (g == 0 || g == N - 1);
 }
 
+// The work of one CTA: cell e, vector block vb of B vectors; thread (v, ty) of
+// a B x nty thread block; smem holds 3 n_q^3 x B values.  Shared by the
+// per-colour launches below and by the persistent batch kernel.
 template <typename T, int NP, int NQ, bool GEN>
-__global__ void __launch_bounds__(256) cell_apply_kernel(const Tables<T, NP, NQ> tab, const MeshDev m,
-                                                         const Geom<T> geo, const int* __restrict__ cells,
-                                                         int n_vec, int n_vb, const T* __restrict__ X,
-                                                         T* __restrict__ Y) {
+__device__ __forceinline__ void cell_body(const Tables<T, NP, NQ>& tab, const MeshDev& m, const Geom<T>& geo, int e,
+                                          int vb, int B, int v, int ty, int nty, int n_vec, const T* __restrict__ X,
+                                          T* __restrict__ Y, T* smem) {
   constexpr int P = NP - 1;
   constexpr int NQ3 = NQ * NQ * NQ;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int B = blockDim.x;
-  T* ST = reinterpret_cast<T*>(smem_raw);
+  T* ST = smem;
   T* S0 = ST + NQ3 * B;
   T* S1 = S0 + NQ3 * B;
-
-  const int v = threadIdx.x, ty = threadIdx.y, nty = blockDim.y;
-  const int vb = blockIdx.x % n_vb;
-  const int e = cells[blockIdx.x / n_vb];
   const int vg = vb * B + v;
   const bool active = vg < n_vec;
   const int cx = e % m.nx, cy = (e / m.nx) % m.ny, cz = e / (m.nx * m.ny);
@@ -272,6 +268,16 @@ __global__ void __launch_bounds__(256) cell_apply_kernel(const Tables<T, NP, NQ>
       else if (!con) *dst += s;
     }
   }
+}
+
+template <typename T, int NP, int NQ, bool GEN>
+__global__ void __launch_bounds__(256) cell_apply_kernel(const Tables<T, NP, NQ> tab, const MeshDev m,
+                                                         const Geom<T> geo, const int* __restrict__ cells,
+                                                         int n_vec, int n_vb, const T* __restrict__ X,
+                                                         T* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cell_body<T, NP, NQ, GEN>(tab, m, geo, cells[blockIdx.x / n_vb], blockIdx.x % n_vb, blockDim.x, threadIdx.x,
+                            threadIdx.y, blockDim.y, n_vec, X, Y, reinterpret_cast<T*>(smem_raw));
 }
 
 // diag(A): one thread per (cell, local node), sum over the quadrature points of

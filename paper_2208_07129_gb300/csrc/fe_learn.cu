@@ -7,10 +7,10 @@
 // its output is scaled back, so z is positively homogeneous in r), w_e the
 // partition-of-unity weights 1 / (number of cells sharing the node), D the
 // diagonal of A.  With W2 = 0 and b2 = 0 the preconditioner is Jacobi.  The
-// network is trained on residual / error pairs (r_k, e_k = x* - x_k) that a
-// Jacobi-PCG solve of the same operator produces, to predict from the patch of
-// r_k the oscillatory part of the patch of e_k - D^-1 r_k (the patch minus the
-// trilinear interpolant of its corner values; mean squared error, Adam).  The paper
+// network is trained on the residual / error trajectory (r_k, e_k = x* - x_k)
+// of a Jacobi-PCG solve of the same operator: by default so that A z(r_k) is
+// close to r_k (the operator itself is in the loss and its gradient), or by
+// patch regression onto the oscillatory part of e_k - D^-1 r_k.  The paper
 // has no learned component; this layer sits on top of its operator.
 //
 // Kernels:
@@ -504,6 +504,112 @@ __global__ void gather_rows_kernel(const float* src, const int* idx, int rows, i
   }
 }
 
+// Operator-in-the-loop objective: inputs of every (cell, column) patch,
+// U[row] = R_e r / s and S[row] = s = ||R_e r||, row = k * ncol + j for cells[k].
+__global__ void gather_inputs_kernel(const MeshDev m, int np, int n3, const int* cells, int ncol,
+                                     const float* __restrict__ r, int nv, float* U, float* S) {
+  __shared__ float red[128];
+  const int k = blockIdx.x;
+  const int e = cells[k / ncol], j = k % ncol;
+  const int cx = e % m.nx, cy = (e / m.nx) % m.ny, cz = e / (m.nx * m.ny);
+  const int P = np - 1;
+  float ss = 0.f;
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+    size_t dof;
+    bool con;
+    float w;
+    node_info(m, P, np, cx, cy, cz, i, &dof, &con, &w);
+    const float v = con ? 0.f : r[dof * nv + j];
+    ss += v * v;
+  }
+  red[threadIdx.x] = ss;
+  __syncthreads();
+  for (int s = 64; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const float sn = sqrtf(red[0]);
+  const float inv = sn > 0.f ? 1.0f / sn : 0.f;
+  if (threadIdx.x == 0) S[k] = sn;
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+    size_t dof;
+    bool con;
+    float w;
+    node_info(m, P, np, cx, cy, cz, i, &dof, &con, &w);
+    U[(size_t)k * n3 + i] = con ? 0.f : r[dof * nv + j] * inv;
+  }
+}
+
+// z += R_e^T (w .* s Y[row])  (training assembly, FP32 atomics)
+__global__ void scatter_outputs_kernel(const MeshDev m, int np, int n3, const int* cells, int ncol, const float* Y,
+                                       const float* S, float* z, int nv) {
+  const int k = blockIdx.x;
+  const int e = cells[k / ncol], j = k % ncol;
+  const int cx = e % m.nx, cy = (e / m.nx) % m.ny, cz = e / (m.nx * m.ny);
+  const float sn = S[k];
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+    size_t dof;
+    bool con;
+    float w;
+    node_info(m, np - 1, np, cx, cy, cz, i, &dof, &con, &w);
+    if (!con) atomicAdd(z + dof * nv + j, w * sn * Y[(size_t)k * n3 + i]);
+  }
+}
+
+// dY[row][i] = s w_i g[dof(e, i)][j]  (adjoint of the assembly)
+__global__ void gather_grad_kernel(const MeshDev m, int np, int n3, const int* cells, int ncol, const float* g,
+                                   const float* S, float* dY, int nv) {
+  const int k = blockIdx.x;
+  const int e = cells[k / ncol], j = k % ncol;
+  const int cx = e % m.nx, cy = (e / m.nx) % m.ny, cz = e / (m.nx * m.ny);
+  const float sn = S[k];
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+    size_t dof;
+    bool con;
+    float w;
+    node_info(m, np - 1, np, cx, cy, cz, i, &dof, &con, &w);
+    dY[(size_t)k * n3 + i] = con ? 0.f : sn * w * g[dof * nv + j];
+  }
+}
+
+// g = (2 / N) (q - r) and partial sums of (q - r)^2
+__global__ void residual_loss_kernel(const float* q, const float* r, float* g, size_t total, float two_over_n,
+                                     float* partial) {
+  __shared__ float red[256];
+  float acc = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const float d = q[i] - r[i];
+    g[i] = two_over_n * d;
+    acc += d * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// dst[:, j] = src[:, j] / ||src[:, j]||  (one CTA per column)
+__global__ void col_normalize_kernel(const float* src, float* dst, size_t n, int nv) {
+  __shared__ float red[256];
+  const int j = blockIdx.x;
+  float acc = 0.f;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float v = src[i * nv + j];
+    acc += v * v;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const float inv = red[0] > 0.f ? rsqrtf(red[0]) : 0.f;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i * nv + j] = src[i * nv + j] * inv;
+}
+
 // err = xs - x  (xs the converged solution)
 __global__ void sub_kernel(const float* xs, const float* x, float* err, size_t total) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
@@ -760,9 +866,90 @@ fe_status pcg_f32_hooked(fe_ctx* c, const float* b, float* x, int nv, const doub
                          cudaStream_t s);
 }
 
+namespace fe {
+// Train by the operator residual: over residual snapshots r (columns scaled to
+// norm 1), minimise mean (A z(r) - r)^2 with z the preconditioner output.
+// The gradient with respect to z is (2/N) A (A z - r) (A symmetric); it is
+// pulled back through the assembly to every patch output and then through the
+// network.  Two FP32 operator applications per step.
+static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder& rec, const int* cells, int nv,
+                                     fe_train_info* inf, cudaStream_t s) {
+  LearnedPrecond* L = c->learned;
+  const int n3 = L->n3;
+  const size_t n = c->n_dofs, tot = n * nv;
+  const size_t rows = c->n_cells * (size_t)nv;
+  TrainBufs tb;
+  float *U = nullptr, *S = nullptr, *rn = nullptr, *z = nullptr, *q = nullptr, *g = nullptr;
+  cudaError_t e = alloc_train(tb, (int)rows, n3);
+  if (e == cudaSuccess) e = cudaMalloc(&U, rows * n3 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&S, rows * sizeof(float));
+  for (float** p : {&rn, &z, &q, &g})
+    if (e == cudaSuccess) e = cudaMalloc(p, tot * sizeof(float));
+  fe_status st = from_cuda(e);
+  const fe_mode saved = c->mode;
+  std::mt19937_64 rng(d->seed + 29);
+  float first = 0.f, last = 0.f, ep_first = 0.f;
+  int step = 0;
+  const int per_epoch = rec.count;
+  for (int ep = 0; ep < d->epochs && st == FE_OK; ++ep) {
+    std::vector<int> order(per_epoch);
+    for (int k = 0; k < per_epoch; ++k) order[k] = k;
+    std::shuffle(order.begin(), order.end(), rng);
+    float ep_loss = 0.f;
+    for (int oi = 0; oi < per_epoch && st == FE_OK; ++oi) {
+      const int k = order[oi];
+      col_normalize_kernel<<<nv, 256, 0, s>>>(rec.r[k], rn, n, nv);
+      gather_inputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, rn, nv, U, S);
+      if ((e = gemm((int)rows, kHidden, n3, U, n3, 1, L->W1, 1, n3, tb.Hpre, s)) != cudaSuccess) break;
+      bias_act_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.Hpre, L->b1, (int)rows, kHidden, 1);
+      if ((e = gemm((int)rows, n3, kHidden, tb.Hpre, kHidden, 1, L->W2, 1, kHidden, tb.Y, s)) != cudaSuccess) break;
+      bias_act_kernel<<<grid_for(rows * n3), 256, 0, s>>>(tb.Y, L->b2, (int)rows, n3, 0);
+      jacobi_init_kernel<<<grid_for(tot), 256, 0, s>>>(rn, c->ws.dinv32, z, n, nv);
+      scatter_outputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, tb.Y, S, z, nv);
+      c->mode = FE_FP32;
+      st = fe_apply(c, z, q, nv, s);
+      if (st == FE_OK) {
+        residual_loss_kernel<<<512, 256, 0, s>>>(q, rn, g, tot, 2.0f / (float)tot, tb.partial);
+        sum_kernel<<<1, 32, 0, s>>>(tb.partial, 512, 1.0f / (float)tot, tb.loss);
+        st = fe_apply(c, g, q, nv, s);   // q <- A g = dL/dz
+      }
+      c->mode = saved;
+      if (st != FE_OK) break;
+      gather_grad_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, q, S, tb.dY, nv);
+      if ((e = gemm(n3, kHidden, (int)rows, tb.dY, 1, n3, tb.Hpre, kHidden, 1, tb.gW2, s)) != cudaSuccess) break;
+      colsum_kernel<<<(n3 + 127) / 128, 128, 0, s>>>(tb.dY, (int)rows, n3, tb.gb2);
+      if ((e = gemm((int)rows, kHidden, n3, tb.dY, n3, 1, L->W2, kHidden, 1, tb.dH, s)) != cudaSuccess) break;
+      relu_grad_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.dH, tb.Hpre, rows * kHidden);
+      if ((e = gemm(kHidden, n3, (int)rows, tb.dH, 1, kHidden, U, n3, 1, tb.gW1, s)) != cudaSuccess) break;
+      colsum_kernel<<<1, 128, 0, s>>>(tb.dH, (int)rows, kHidden, tb.gb1);
+      adam_step(L, tb, d->lr, s);
+      float h = 0.f;
+      cudaMemcpyAsync(&h, tb.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+      if (step == 0) first = h;
+      ep_loss += h;
+      ++step;
+    }
+    if (e != cudaSuccess && st == FE_OK) st = from_cuda(e);
+    last = per_epoch ? ep_loss / per_epoch : 0.f;
+    if (ep == 0) ep_first = last;
+  }
+  c->mode = saved;
+  inf->loss_first_step = first;
+  inf->loss_first_epoch = ep_first;
+  inf->loss_last_epoch = last;
+  inf->steps = step;
+  inf->samples = (long long)rows * rec.count;
+  free_train(tb);
+  for (float* p : {U, S, rn, z, q, g}) cudaFree(p);
+  return st;
+}
+}  // namespace fe
+
 extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_train_info* info, void* stream) {
   if (!c || !d || d->n_rhs <= 0 || d->snapshots <= 0 || d->snapshot_every <= 0 || d->epochs < 0 || d->batch <= 0 ||
-      !(d->lr > 0.f) || !(d->traj_rtol > 0.0))
+      !(d->lr > 0.f) || !(d->traj_rtol > 0.0) ||
+      (d->objective != FE_TRAIN_OPERATOR_RESIDUAL && d->objective != FE_TRAIN_PATCH_ERROR))
     return FE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t t0, t1;
@@ -801,7 +988,7 @@ extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_trai
   std::vector<int> hcells(c->n_cells);
   for (size_t k = 0; k < c->n_cells; ++k) hcells[k] = (int)k;
   const size_t per_snap = c->n_cells * (size_t)nv;
-  const size_t samples = per_snap * d->snapshots;
+  const size_t samples = d->objective == FE_TRAIN_PATCH_ERROR ? per_snap * d->snapshots : 1;
   e = cudaMalloc(&b, tot * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&x, tot * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&err, tot * sizeof(float));
@@ -836,10 +1023,12 @@ extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_trai
     st = pcg_f32_hooked(c, b, x, nv, tol.data(), 200000, record_hook, &rec, &its, s);
     inf.trajectory_iterations = its;
   }
-  // samples: U = R_e r_k / s, T = R_e (x* - x_k - D^-1 r_k) / s
+  const bool patch_mode = d->objective == FE_TRAIN_PATCH_ERROR;
+  if (st == FE_OK && !patch_mode) st = train_operator_loss(c, d, rec, cells, nv, &inf, s);
+  // patch regression: U = R_e r_k / s, T = HF(R_e (x* - x_k - D^-1 r_k)) / s
   Gll gll{};
   for (int i = 0; i < c->np && i < 16; ++i) gll.x[i] = (float)c->gll[i];
-  if (st == FE_OK) {
+  if (st == FE_OK && patch_mode) {
     for (int k = 0; k < rec.count; ++k) {
       sub_kernel<<<grid_for(tot), 256, 0, s>>>(x, rec.x[k], err, tot);
       gather_samples_kernel<<<(unsigned)per_snap, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, rec.r[k], err,
@@ -847,10 +1036,10 @@ extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_trai
     }
     if ((e = cudaGetLastError()) != cudaSuccess) st = from_cuda(e);
   }
-  const size_t nsamp = per_snap * rec.count;
-  inf.samples = (long long)nsamp;
+  const size_t nsamp = patch_mode ? per_snap * rec.count : 0;
+  if (patch_mode) inf.samples = (long long)nsamp;
   // Adam epochs over shuffled mini-batches
-  if (st == FE_OK && nsamp > 0) {
+  if (st == FE_OK && patch_mode && nsamp > 0) {
     std::mt19937_64 rng(d->seed + 17);
     std::vector<int> perm(nsamp);
     for (size_t i = 0; i < nsamp; ++i) perm[i] = (int)i;

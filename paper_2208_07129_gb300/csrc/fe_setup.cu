@@ -379,7 +379,7 @@ extern "C" fe_mode fe_get_mode(const fe_ctx* c) { return c ? c->mode : FE_FP64; 
 
 extern "C" fe_status fe_set_tile(fe_ctx* c, fe_mode mode, int vectors_per_cta, int lines, int variant) {
   if (!c || vectors_per_cta < 1 || vectors_per_cta > 32 || (vectors_per_cta & (vectors_per_cta - 1)) != 0 ||
-      lines < 1 || lines > 32 || variant < 0 || variant > 2)
+      lines < 1 || lines > 256 || variant < 0 || variant > 2)
     return FE_EINVAL;
   if (mode == FE_FP64) {
     if (variant == 2) return FE_EINVAL;

@@ -49,13 +49,23 @@ PRECONDS = {"none": FE_PRECOND_NONE, "jacobi": FE_PRECOND_JACOBI, "learned": FE_
 class fe_train_desc(ctypes.Structure):
     _fields_ = [("n_rhs", ctypes.c_int), ("snapshots", ctypes.c_int), ("snapshot_every", ctypes.c_int),
                 ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
-                ("traj_rtol", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+                ("traj_rtol", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("objective", ctypes.c_int)]
+
+
+FE_TRAIN_OPERATOR_RESIDUAL, FE_TRAIN_PATCH_ERROR = 0, 1
+OBJECTIVES = {"operator": FE_TRAIN_OPERATOR_RESIDUAL, "patch_error": FE_TRAIN_PATCH_ERROR}
 
 
 class fe_train_info(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_longlong), ("steps", ctypes.c_int), ("trajectory_iterations", ctypes.c_int),
                 ("loss_first_step", ctypes.c_float), ("loss_first_epoch", ctypes.c_float),
                 ("loss_last_epoch", ctypes.c_float), ("seconds", ctypes.c_double)]
+
+
+class fe_batch_info(ctypes.Structure):
+    _fields_ = [("problems", ctypes.c_int), ("work_items", ctypes.c_int), ("phases", ctypes.c_int),
+                ("grid", ctypes.c_int), ("smem_bytes", ctypes.c_longlong), ("autotune_ms", ctypes.c_float),
+                ("device_status", ctypes.c_int)]
 
 
 class fe_quad_desc(ctypes.Structure):
@@ -95,6 +105,12 @@ def lib() -> ctypes.CDLL:
         "fe_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "fe_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "fe_precond_init": (ctypes.c_int, [_VP, ctypes.c_ulonglong]),
+        "fe_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
+        "fe_batch_apply": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+        "fe_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(fe_batch_info), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+        "fe_batch_destroy": (None, [_VP]),
         "fe_precond_train": (ctypes.c_int, [_VP, ctypes.POINTER(fe_train_desc), ctypes.POINTER(fe_train_info), _VP]),
         "fe_precond_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
         "fe_precond_set_weights": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
@@ -286,8 +302,8 @@ def fe_precond_get_weights(ctx: int):
 
 
 def fe_precond_train(ctx: int, n_rhs=8, snapshots=8, snapshot_every=25, epochs=4, batch=4096, lr=1e-3,
-                     traj_rtol=1e-6, seed=0, stream=None) -> dict:
-    d = fe_train_desc(n_rhs, snapshots, snapshot_every, epochs, batch, lr, traj_rtol, seed)
+                     traj_rtol=1e-6, seed=0, objective="operator", stream=None) -> dict:
+    d = fe_train_desc(n_rhs, snapshots, snapshot_every, epochs, batch, lr, traj_rtol, seed, OBJECTIVES[objective])
     info = fe_train_info()
     _check(lib().fe_precond_train(ctx, ctypes.byref(d), ctypes.byref(info), _stream_ptr(stream)), "fe_precond_train")
     return {f: getattr(info, f) for f, _ in fe_train_info._fields_}
@@ -321,6 +337,38 @@ def fe_mlp_gradients(ctx: int, U, T, stream=None):
     _check(lib().fe_mlp_gradients(ctx, U.data_ptr(), T.data_ptr(), U.shape[0], loss.data_ptr(),
                                   *[x.data_ptr() for x in g], _stream_ptr(stream)), "fe_mlp_gradients")
     return loss, g
+
+
+def fe_batch_create(ctxs, n_vec, mode="fp64", autotune=True) -> int:
+    n = len(ctxs)
+    arr = (_VP * n)(*ctxs)
+    nv = (ctypes.c_int * n)(*n_vec)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    out = _VP()
+    _check(lib().fe_batch_create(arr, n, nv, m, int(bool(autotune)), ctypes.byref(out)), "fe_batch_create")
+    return out.value
+
+
+def fe_batch_apply(batch: int, X, Y, stream=None) -> None:
+    n = len(X)
+    xs = (_VP * n)(*[t.data_ptr() for t in X])
+    ys = (_VP * n)(*[t.data_ptr() for t in Y])
+    _check(lib().fe_batch_apply(batch, xs, ys, _stream_ptr(stream)), "fe_batch_apply")
+
+
+def fe_batch_stats(batch: int, n: int) -> dict:
+    info = fe_batch_info()
+    vb = (ctypes.c_int * n)()
+    cb = (ctypes.c_int * n)()
+    _check(lib().fe_batch_stats(batch, ctypes.byref(info), vb, cb), "fe_batch_stats")
+    d = {f: getattr(info, f) for f, _ in fe_batch_info._fields_}
+    d["vectors_per_cta"] = list(vb)
+    d["cells_per_item"] = list(cb)
+    return d
+
+
+def fe_batch_destroy(batch: int) -> None:
+    lib().fe_batch_destroy(batch)
 
 
 def fe_last_device_status(ctx: int) -> int:
