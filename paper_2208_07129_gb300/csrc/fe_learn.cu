@@ -8,9 +8,11 @@
 // partition-of-unity weights 1 / (number of cells sharing the node), D the
 // diagonal of A.  With W2 = 0 and b2 = 0 the preconditioner is Jacobi.  The
 // network is trained on the residual / error trajectory (r_k, e_k = x* - x_k)
-// of a Jacobi-PCG solve of the same operator: by default so that A z(r_k) is
-// close to r_k (the operator itself is in the loss and its gradient), or by
-// patch regression onto the oscillatory part of e_k - D^-1 r_k.  The paper
+// of a Jacobi-PCG solve of the same operator.  Default objective: the energy
+// norm of what the preconditioner misses, mean ||e_k - z(r_k)||_A^2 -- the
+// norm CG minimises -- with the operator itself in the loss and its gradient;
+// alternatives: the operator residual ||A z(r_k) - r_k||^2, or patch
+// regression onto the oscillatory part of e_k - D^-1 r_k.  The paper
 // has no learned component; this layer sits on top of its operator.
 //
 // Kernels:
@@ -610,6 +612,51 @@ __global__ void col_normalize_kernel(const float* src, float* dst, size_t n, int
   for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i * nv + j] = src[i * nv + j] * inv;
 }
 
+// scale[j] = 1 / ||src[:, j]||  (one CTA per column)
+__global__ void col_invnorm_kernel(const float* src, float* scale, size_t n, int nv) {
+  __shared__ float red[256];
+  const int j = blockIdx.x;
+  float acc = 0.f;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float v = src[i * nv + j];
+    acc += v * v;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) scale[j] = red[0] > 0.f ? rsqrtf(red[0]) : 0.f;
+}
+
+// dst = scale_col .* src ; if sub != nullptr: dst = scale_col .* (sub - src)
+__global__ void col_scale_kernel(const float* src, const float* sub, const float* scale, float* dst, size_t total,
+                                 int nv) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = sub ? sub[i] - src[i] : src[i];
+    dst[i] = scale[i % nv] * v;
+  }
+}
+
+// energy objective: g = (2 / N) q with q = A d, partial sums of d . q
+__global__ void energy_loss_kernel(const float* d, const float* q, float* g, size_t total, float two_over_n,
+                                   float* partial) {
+  __shared__ float red[256];
+  float acc = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    g[i] = two_over_n * q[i];
+    acc += d[i] * q[i];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
 // err = xs - x  (xs the converged solution)
 __global__ void sub_kernel(const float* xs, const float* x, float* err, size_t total) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
@@ -861,33 +908,88 @@ extern "C" fe_status fe_mlp_gradients(fe_ctx* c, const float* U, const float* T,
 }
 
 namespace fe {
+fe_status pcg_f32(fe_ctx* c, const float* b, float* x, int nv, const double* tol, int max_it, int precond, int* its,
+                  cudaStream_t s);
 fe_status pcg_f32_hooked(fe_ctx* c, const float* b, float* x, int nv, const double* tol, int max_it,
                          void (*hook)(void*, int, const void*, const void*, cudaStream_t), void* user, int* its,
                          cudaStream_t s);
 }
 
 namespace fe {
+// Held-out check used to pick the training checkpoint: iterations of an FP32
+// block PCG with the given preconditioner on fixed validation right-hand sides
+// (relative tolerance tol, capped at max_it).
+struct Validation {
+  float *b = nullptr, *x = nullptr;
+  int nv = 0;
+  std::vector<double> tol;
+};
+
+static int validate(fe_ctx* c, Validation& v, int precond, int max_it, cudaStream_t s) {
+  cudaMemsetAsync(v.x, 0, c->n_dofs * (size_t)v.nv * sizeof(float), s);
+  int its = 0;
+  fe_status st = pcg_f32(c, v.b, v.x, v.nv, v.tol.data(), max_it, precond, &its, s);
+  return st == FE_OK ? its : max_it + 1;
+}
+
+struct Checkpoint {
+  float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
+};
+
+static void copy_weights(LearnedPrecond* L, float* W1, float* b1, float* W2, float* b2, bool to_ckpt, cudaStream_t s) {
+  const size_t w = (size_t)kHidden * L->n3;
+  auto cp = [&](float* ck, float* live, size_t n) {
+    if (to_ckpt) cudaMemcpyAsync(ck, live, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    else cudaMemcpyAsync(live, ck, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  };
+  cp(W1, L->W1, w);
+  cp(b1, L->b1, kHidden);
+  cp(W2, L->W2, w);
+  cp(b2, L->b2, L->n3);
+}
+
 // Train by the operator residual: over residual snapshots r (columns scaled to
 // norm 1), minimise mean (A z(r) - r)^2 with z the preconditioner output.
 // The gradient with respect to z is (2/N) A (A z - r) (A symmetric); it is
 // pulled back through the assembly to every patch output and then through the
 // network.  Two FP32 operator applications per step.
 static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder& rec, const int* cells, int nv,
-                                     fe_train_info* inf, cudaStream_t s) {
+                                     fe_train_info* inf, cudaStream_t s, const float* xstar, Validation& val) {
+  const bool energy = d->objective == FE_TRAIN_ENERGY;
   LearnedPrecond* L = c->learned;
   const int n3 = L->n3;
   const size_t n = c->n_dofs, tot = n * nv;
   const size_t rows = c->n_cells * (size_t)nv;
   TrainBufs tb;
-  float *U = nullptr, *S = nullptr, *rn = nullptr, *z = nullptr, *q = nullptr, *g = nullptr;
+  float *U = nullptr, *S = nullptr, *rn = nullptr, *z = nullptr, *q = nullptr, *g = nullptr, *en = nullptr,
+        *cs = nullptr;
   cudaError_t e = alloc_train(tb, (int)rows, n3);
   if (e == cudaSuccess) e = cudaMalloc(&U, rows * n3 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&S, rows * sizeof(float));
-  for (float** p : {&rn, &z, &q, &g})
+  if (e == cudaSuccess) e = cudaMalloc(&cs, nv * sizeof(float));
+  for (float** p : {&rn, &z, &q, &g, &en})
     if (e == cudaSuccess) e = cudaMalloc(p, tot * sizeof(float));
   fe_status st = from_cuda(e);
   const fe_mode saved = c->mode;
   std::mt19937_64 rng(d->seed + 29);
+  // checkpoints: epoch 0 is the network with a zero output layer (exactly Jacobi)
+  Checkpoint best;
+  const size_t wsz = (size_t)kHidden * n3;
+  if (st == FE_OK) {
+    e = cudaMalloc(&best.W1, wsz * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&best.b1, kHidden * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&best.W2, wsz * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&best.b2, n3 * sizeof(float));
+    st = from_cuda(e);
+  }
+  int val_jac = 0, best_its = 0, best_epoch = 0;
+  if (st == FE_OK && val.nv > 0) {
+    val_jac = validate(c, val, FE_PRECOND_JACOBI, 100000, s);
+    best_its = val_jac;
+    copy_weights(L, best.W1, best.b1, best.W2, best.b2, true, s);
+    cudaMemsetAsync(best.W2, 0, wsz * sizeof(float), s);
+    cudaMemsetAsync(best.b2, 0, n3 * sizeof(float), s);
+  }
   float first = 0.f, last = 0.f, ep_first = 0.f;
   int step = 0;
   const int per_epoch = rec.count;
@@ -898,7 +1000,10 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
     float ep_loss = 0.f;
     for (int oi = 0; oi < per_epoch && st == FE_OK; ++oi) {
       const int k = order[oi];
-      col_normalize_kernel<<<nv, 256, 0, s>>>(rec.r[k], rn, n, nv);
+      // r_k and e_k = x* - x_k scaled by 1 / ||r_k|| per column
+      col_invnorm_kernel<<<nv, 256, 0, s>>>(rec.r[k], cs, n, nv);
+      col_scale_kernel<<<grid_for(tot), 256, 0, s>>>(rec.r[k], nullptr, cs, rn, tot, nv);
+      if (energy) col_scale_kernel<<<grid_for(tot), 256, 0, s>>>(rec.x[k], xstar, cs, en, tot, nv);
       gather_inputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, rn, nv, U, S);
       if ((e = gemm((int)rows, kHidden, n3, U, n3, 1, L->W1, 1, n3, tb.Hpre, s)) != cudaSuccess) break;
       bias_act_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.Hpre, L->b1, (int)rows, kHidden, 1);
@@ -907,11 +1012,22 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
       jacobi_init_kernel<<<grid_for(tot), 256, 0, s>>>(rn, c->ws.dinv32, z, n, nv);
       scatter_outputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, tb.Y, S, z, nv);
       c->mode = FE_FP32;
-      st = fe_apply(c, z, q, nv, s);
-      if (st == FE_OK) {
-        residual_loss_kernel<<<512, 256, 0, s>>>(q, rn, g, tot, 2.0f / (float)tot, tb.partial);
-        sum_kernel<<<1, 32, 0, s>>>(tb.partial, 512, 1.0f / (float)tot, tb.loss);
-        st = fe_apply(c, g, q, nv, s);   // q <- A g = dL/dz
+      if (energy) {
+        // loss = (z - e)^T A (z - e) / N, dL/dz = 2 A (z - e) / N
+        sub_kernel<<<grid_for(tot), 256, 0, s>>>(z, en, g, tot);
+        st = fe_apply(c, g, q, nv, s);
+        if (st == FE_OK) {
+          energy_loss_kernel<<<512, 256, 0, s>>>(g, q, rn, tot, 2.0f / (float)tot, tb.partial);
+          sum_kernel<<<1, 32, 0, s>>>(tb.partial, 512, 1.0f / (float)tot, tb.loss);
+          std::swap(q, rn);   // the gradient dL/dz now sits in q (rn is rebuilt next step)
+        }
+      } else {
+        st = fe_apply(c, z, q, nv, s);
+        if (st == FE_OK) {
+          residual_loss_kernel<<<512, 256, 0, s>>>(q, rn, g, tot, 2.0f / (float)tot, tb.partial);
+          sum_kernel<<<1, 32, 0, s>>>(tb.partial, 512, 1.0f / (float)tot, tb.loss);
+          st = fe_apply(c, g, q, nv, s);   // q <- A g = dL/dz
+        }
       }
       c->mode = saved;
       if (st != FE_OK) break;
@@ -933,15 +1049,29 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
     if (e != cudaSuccess && st == FE_OK) st = from_cuda(e);
     last = per_epoch ? ep_loss / per_epoch : 0.f;
     if (ep == 0) ep_first = last;
+    if (st == FE_OK && val.nv > 0) {
+      if ((e = refresh_images(c, s)) != cudaSuccess) { st = from_cuda(e); break; }
+      const int its = validate(c, val, FE_PRECOND_LEARNED, 2 * val_jac + 10, s);
+      if (its < best_its) {
+        best_its = its;
+        best_epoch = ep + 1;
+        copy_weights(L, best.W1, best.b1, best.W2, best.b2, true, s);
+      }
+    }
   }
   c->mode = saved;
+  if (st == FE_OK && val.nv > 0) copy_weights(L, best.W1, best.b1, best.W2, best.b2, false, s);
+  inf->val_jacobi_iterations = val_jac;
+  inf->val_learned_iterations = best_its;
+  inf->best_epoch = best_epoch;
+  for (float* p : {best.W1, best.b1, best.W2, best.b2}) cudaFree(p);
   inf->loss_first_step = first;
   inf->loss_first_epoch = ep_first;
   inf->loss_last_epoch = last;
   inf->steps = step;
   inf->samples = (long long)rows * rec.count;
   free_train(tb);
-  for (float* p : {U, S, rn, z, q, g}) cudaFree(p);
+  for (float* p : {U, S, rn, z, q, g, en, cs}) cudaFree(p);
   return st;
 }
 }  // namespace fe
@@ -949,7 +1079,8 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
 extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_train_info* info, void* stream) {
   if (!c || !d || d->n_rhs <= 0 || d->snapshots <= 0 || d->snapshot_every <= 0 || d->epochs < 0 || d->batch <= 0 ||
       !(d->lr > 0.f) || !(d->traj_rtol > 0.0) ||
-      (d->objective != FE_TRAIN_OPERATOR_RESIDUAL && d->objective != FE_TRAIN_PATCH_ERROR))
+      (d->objective != FE_TRAIN_OPERATOR_RESIDUAL && d->objective != FE_TRAIN_PATCH_ERROR &&
+       d->objective != FE_TRAIN_ENERGY))
     return FE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t t0, t1;
@@ -1024,7 +1155,34 @@ extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_trai
     inf.trajectory_iterations = its;
   }
   const bool patch_mode = d->objective == FE_TRAIN_PATCH_ERROR;
-  if (st == FE_OK && !patch_mode) st = train_operator_loss(c, d, rec, cells, nv, &inf, s);
+  Validation val;
+  if (st == FE_OK && !patch_mode && d->n_val > 0) {
+    // held-out right-hand sides (their own seed), relative tolerance 1e-6
+    val.nv = std::min(d->n_val, nv);
+    std::vector<float> hv(n * (size_t)val.nv);
+    std::mt19937_64 vr(d->seed ^ 0xD1B54A32D192ED03ULL);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    std::vector<double> bn(val.nv, 0.0);
+    const int Nx = c->mdev.Nx, Ny = c->mdev.Ny, Nz = c->mdev.Nz;
+    for (size_t i = 0; i < n; ++i) {
+      const int gx = (int)(i % Nx), gy = (int)((i / Nx) % Ny), gz = (int)(i / ((size_t)Nx * Ny));
+      const bool con = !c->periodic && (gx == 0 || gy == 0 || gz == 0 || gx == Nx - 1 || gy == Ny - 1 || gz == Nz - 1);
+      for (int j = 0; j < val.nv; ++j) {
+        const float v = con ? 0.f : nd(vr);
+        hv[i * val.nv + j] = v;
+        bn[j] += (double)v * v;
+      }
+    }
+    val.tol.resize(val.nv);
+    for (int j = 0; j < val.nv; ++j) val.tol[j] = 1e-6 * std::sqrt(bn[j]);
+    e = cudaMalloc(&val.b, hv.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&val.x, hv.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(val.b, hv.data(), hv.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = from_cuda(e);
+  }
+  if (st == FE_OK && !patch_mode) st = train_operator_loss(c, d, rec, cells, nv, &inf, s, x, val);
+  cudaFree(val.b);
+  cudaFree(val.x);
   // patch regression: U = R_e r_k / s, T = HF(R_e (x* - x_k - D^-1 r_k)) / s
   Gll gll{};
   for (int i = 0; i < c->np && i < 16; ++i) gll.x[i] = (float)c->gll[i];

@@ -348,6 +348,16 @@ fe_status pcg_f32_hooked(fe_ctx* c, const float* b, float* x, int nv, const doub
   return st;
 }
 
+fe_status pcg_f32(fe_ctx* c, const float* b, float* x, int nv, const double* tol, int max_it, int precond, int* its,
+                  cudaStream_t s) {
+  SolveWs& w = c->ws;
+  const fe_mode saved = c->inner_mode;
+  c->inner_mode = FE_FP32;
+  fe_status st = pcg<float>(c, b, x, nv, tol, max_it, precond, s, w.v32[0], w.v32[1], w.v32[2], w.v32[5], its, 4);
+  c->inner_mode = saved;
+  return st;
+}
+
 void free_solver_workspace(fe_ctx* c) {
   SolveWs& w = c->ws;
   for (int k = 0; k < 4; ++k) cudaFree(w.v64[k]);

@@ -49,17 +49,20 @@ PRECONDS = {"none": FE_PRECOND_NONE, "jacobi": FE_PRECOND_JACOBI, "learned": FE_
 class fe_train_desc(ctypes.Structure):
     _fields_ = [("n_rhs", ctypes.c_int), ("snapshots", ctypes.c_int), ("snapshot_every", ctypes.c_int),
                 ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
-                ("traj_rtol", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("objective", ctypes.c_int)]
+                ("traj_rtol", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("objective", ctypes.c_int),
+                ("n_val", ctypes.c_int)]
 
 
-FE_TRAIN_OPERATOR_RESIDUAL, FE_TRAIN_PATCH_ERROR = 0, 1
-OBJECTIVES = {"operator": FE_TRAIN_OPERATOR_RESIDUAL, "patch_error": FE_TRAIN_PATCH_ERROR}
+FE_TRAIN_OPERATOR_RESIDUAL, FE_TRAIN_PATCH_ERROR, FE_TRAIN_ENERGY = 0, 1, 2
+OBJECTIVES = {"operator": FE_TRAIN_OPERATOR_RESIDUAL, "patch_error": FE_TRAIN_PATCH_ERROR, "energy": FE_TRAIN_ENERGY}
 
 
 class fe_train_info(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_longlong), ("steps", ctypes.c_int), ("trajectory_iterations", ctypes.c_int),
                 ("loss_first_step", ctypes.c_float), ("loss_first_epoch", ctypes.c_float),
-                ("loss_last_epoch", ctypes.c_float), ("seconds", ctypes.c_double)]
+                ("loss_last_epoch", ctypes.c_float), ("seconds", ctypes.c_double),
+                ("val_jacobi_iterations", ctypes.c_int), ("val_learned_iterations", ctypes.c_int),
+                ("best_epoch", ctypes.c_int)]
 
 
 class fe_batch_info(ctypes.Structure):
@@ -302,8 +305,9 @@ def fe_precond_get_weights(ctx: int):
 
 
 def fe_precond_train(ctx: int, n_rhs=8, snapshots=8, snapshot_every=25, epochs=4, batch=4096, lr=1e-3,
-                     traj_rtol=1e-6, seed=0, objective="operator", stream=None) -> dict:
-    d = fe_train_desc(n_rhs, snapshots, snapshot_every, epochs, batch, lr, traj_rtol, seed, OBJECTIVES[objective])
+                     traj_rtol=1e-6, seed=0, objective="energy", n_val=4, stream=None) -> dict:
+    d = fe_train_desc(n_rhs, snapshots, snapshot_every, epochs, batch, lr, traj_rtol, seed, OBJECTIVES[objective],
+                      n_val)
     info = fe_train_info()
     _check(lib().fe_precond_train(ctx, ctypes.byref(d), ctypes.byref(info), _stream_ptr(stream)), "fe_precond_train")
     return {f: getattr(info, f) for f, _ in fe_train_info._fields_}
