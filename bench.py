@@ -141,13 +141,21 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """Max of a per-rank scalar (timings: the slowest rank defines the step)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_throughput(units_per_rank: int, ms_per_step: float, world: int) -> float:
+    """Whole-job throughput in G units/s: every rank processes its own copy of
+    the workload (weak scaling), the step takes the slowest rank's time."""
+    return units_per_rank * world / (ms_per_step * 1e-3) / 1e9
 
 
 def traffic_for(kernel: str, source_files):
@@ -171,46 +179,69 @@ def traffic_for(kernel: str, source_files):
 KERNEL_SOURCES = ["paper_2208_07129_gb300/csrc/fe_cell_kernel.cuh", "paper_2208_07129_gb300/csrc/fe_dispatch.cuh"]
 
 
+class OracleSample:
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the workload: rows of A X, each row assembled from its cell matrices by
+    FP64 quadrature and multiplied with the vector block."""
+
+    def __init__(self, w):
+        from oracle import oracle as orc
+        self.orc, self.w = orc, w
+        self.mesh = orc.Mesh(w.nx, w.ny, w.nz, periodic=w.periodic, vertices=w.vertices())
+        self.Vo = w.potential_at(orc.quad_points(self.mesh, w.p, w.nq))
+        self.X = inputs.random_block(w.num_dofs, w.n_vec, w.x_dist, w.x_seed)
+        self.rng = np.random.default_rng(0)
+        self.rows_per_s = None
+
+    def run(self, n_rows: int) -> float:
+        rows = np.sort(self.rng.integers(0, self.w.num_dofs, n_rows))
+        t0 = time.perf_counter()
+        self.orc.apply_rows(self.mesh, self.w.p, self.w.nq, self.X, rows, Vq=self.Vo, mu=self.w.mu)
+        dt = time.perf_counter() - t0
+        self.rows_per_s = n_rows / dt
+        return dt
+
+    def sized(self, budget_s: float) -> int:
+        if self.rows_per_s is None:
+            self.run(8 * self.orc.num_threads())
+        return max(8, int(self.rows_per_s * budget_s))
+
+    def result(self, n_rows: int, dt: float) -> dict:
+        w = self.w
+        return {"value": n_rows * w.n_vec / dt / 1e9, "unit": UNIT, "cores": self.orc.num_threads(), "kind": "oracle",
+                "sample": f"{n_rows} of {w.num_dofs} rows of A X ({w.name}), each row assembled from its cell "
+                          f"matrices by FP64 quadrature and multiplied with the {w.n_vec}-vector block; {dt:.1f} s"}
+
+
 def cpu_baseline(w, budget_s: float = 12.0):
-    """The FP64 oracle as it stands, on the host cores: rows of A X for this
-    workload, each row assembled from its cell matrices and multiplied with X."""
-    from oracle import oracle as orc
-    mesh = orc.Mesh(w.nx, w.ny, w.nz, periodic=w.periodic, vertices=w.vertices())
-    Vo = w.potential_at(orc.quad_points(mesh, w.p, w.nq))
-    rng = np.random.default_rng(0)
-    n = w.num_dofs
-    X = inputs.random_block(n, w.n_vec, w.x_dist, w.x_seed)
-    probe = np.sort(rng.integers(0, n, 8 * orc.num_threads()))
-    t0 = time.perf_counter()
-    orc.apply_rows(mesh, w.p, w.nq, X, probe, Vq=Vo, mu=w.mu)
-    dt = time.perf_counter() - t0
-    rows_n = max(len(probe), int(len(probe) * budget_s / max(dt, 1e-3)))
-    rows = np.sort(rng.integers(0, n, rows_n))
-    t0 = time.perf_counter()
-    orc.apply_rows(mesh, w.p, w.nq, X, rows, Vq=Vo, mu=w.mu)
-    dt = time.perf_counter() - t0
-    return {"value": len(rows) * w.n_vec / dt / 1e9, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
-            "sample": f"{len(rows)} of {n} rows of A X ({w.name}), each row assembled from its cell matrices "
-                      f"by FP64 quadrature and multiplied with the {w.n_vec}-vector block; {dt:.1f} s"}
+    o = OracleSample(w)
+    n = o.sized(budget_s)
+    return o.result(n, o.run(n))
 
 
 def run_reference(args):
-    world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only); each
+    step is a bounded sample of rows of the 32^3 workload."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = inputs.WORKLOADS["c2"]
-    per_step = []
-    cb = None
-    for s in range(args.warmup + args.steps):
-        cb = cpu_baseline(w, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
-        if s >= args.warmup:
-            per_step.append(cb["value"])
-    v = statistics.median(per_step)
+    o = OracleSample(w)
+    n = o.sized(max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+    for _ in range(args.warmup):
+        o.run(n)
+    vals, dts = [], []
+    for _ in range(args.steps):
+        dt = o.run(n)
+        dts.append(dt)
+        vals.append(n * w.n_vec / dt / 1e9)
+    v = statistics.median(vals)
+    cb = o.result(n, statistics.median(dts))
     cb["value"] = v
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": w.name, "dofs": w.num_dofs, "n_vec": w.n_vec},
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(dts) * 1e3,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": w.name, "dofs": w.num_dofs, "n_vec": w.n_vec},
                       "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                                   "d2h_bytes_per_step": 0}}), flush=True)
 
@@ -273,8 +304,78 @@ def solve_bench(fe, torch, sub_cols: int = 16):
                               "seconds_extrapolated": rs["iterations"] * t_it + (t[2] - 2 * t_it),
                               "extrapolated": True}
         out["speedup_mixed_vs_fp64"] = out["fp64_jacobi"]["seconds_extrapolated"] / r["seconds"]
+        # learned cell-patch preconditioner: trained on this operator's own Jacobi-PCG
+        # trajectories (16 random right-hand sides, energy-norm objective, checkpoint
+        # picked on 4 held-out right-hand sides), then used inside the mixed solve
+        info = fe.fe_precond_train(ctx, n_rhs=16, snapshots=16, snapshot_every=10, epochs=12, batch=2048, lr=1e-3,
+                                   traj_rtol=1e-6, seed=3, objective="energy", n_val=4)
+        X.zero_()
+        rl = fe.fe_solve(ctx, Bd, X, rtol=1e-8, max_it=50000, precond="learned", inner_mode="fp32")
+        rl.pop("rel_res")
+        out["mixed_fp32_learned"] = rl
+        out["training"] = info
+        out["learned_vs_jacobi_iterations"] = rl["iterations"] / max(1, r["iterations"])
+        out["speedup_learned_vs_fp64"] = out["fp64_jacobi"]["seconds_extrapolated"] / rl["seconds"]
     finally:
         fe.fe_destroy(ctx)
+    return out
+
+
+def batch_bench(fe, torch, steps: int = 2):
+    """The uneven batch: 24 periodic problems (n ~ U{4..24}, p ~ U{3..8},
+    n_vec log-uniform in [8, 512]) in FP64, one persistent launch per apply
+    replayed from a CUDA graph, against the same problems applied one after
+    another with their own launches."""
+    ws = inputs.batch_workloads()
+    ctxs, Xs, Ys = [], [], []
+    out = {"problems": len(ws), "mode": "fp64"}
+    try:
+        for w in ws:
+            ctx = fe.setup_workload(w)
+            ctxs.append(ctx)
+            X = torch.from_numpy(w.make_x()).cuda()
+            Xs.append(X)
+            Ys.append(torch.empty_like(X))
+        units = sum(w.num_dofs * w.n_vec for w in ws)
+        flops = sum(flops_per_cell_vec(w.p + 1, w.nq) * w.num_cells * w.n_vec for w in ws)
+        b = fe.fe_batch_create(ctxs, [w.n_vec for w in ws], mode="fp64", autotune=True)
+        try:
+            st = fe.fe_batch_stats(b, len(ws))
+            fe.fe_batch_apply(b, Xs, Ys)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                fe.fe_batch_apply(b, Xs, Ys)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_b = e0.elapsed_time(e1) / steps
+            st2 = fe.fe_batch_stats(b, len(ws))
+        finally:
+            fe.fe_batch_destroy(b)
+        Yr = [torch.empty_like(y) for y in Ys]
+        for c, X, Y in zip(ctxs, Xs, Yr):
+            fe.fe_apply(c, X, Y)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            for c, X, Y in zip(ctxs, Xs, Yr):
+                fe.fe_apply(c, X, Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / steps
+        same = all(torch.equal(a, c) for a, c in zip(Ys, Yr))
+        out.update({"dofs_x_vectors": units, "ms_per_batch_apply": ms_b, "value": units / (ms_b * 1e-3) / 1e9,
+                    "unit": UNIT, "tflops": flops / (ms_b * 1e-3) / 1e12,
+                    "ms_per_problem_launches": ms_s, "speedup_vs_per_problem_launches": ms_s / ms_b,
+                    "bitwise_equal_to_per_problem": same, "device_status": st2["device_status"],
+                    "work_items": st["work_items"], "phases": st["phases"], "grid": st["grid"],
+                    "autotune_ms": st["autotune_ms"], "vectors_per_cta": st["vectors_per_cta"],
+                    "cells_per_item": st["cells_per_item"],
+                    "shapes": [[w.nx, w.p, w.n_vec] for w in ws]})
+    finally:
+        for c in ctxs:
+            fe.fe_destroy(c)
     return out
 
 
@@ -288,6 +389,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--modes", default="fp64,fp32")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -311,6 +413,7 @@ def main():
 
     modes = {}
     want = args.modes.split(",")
+    extra_modes = [m for m in ("tf32", "bf16") if m in want or args.modes == "fp64,fp32"]
     with ClockSampler(local) as clk:
         ms64 = ms32 = float("nan")
         X64 = Y64 = X32 = Y32 = None
@@ -318,6 +421,10 @@ def main():
             ms64, per64, X64, Y64 = time_mode(fe, torch, ctx, w, "fp64", args.steps, max(3, args.warmup), world)
         if "fp32" in want:
             ms32, per32, X32, Y32 = time_mode(fe, torch, ctx, w, "fp32", args.steps, max(3, args.warmup), world)
+        ms_tc = {}
+        for m in extra_modes:
+            ms_tc[m], _, Xt, Yt = time_mode(fe, torch, ctx, w, m, args.steps, max(3, args.warmup), world)
+            ms_tc[m + "_sample"] = (Xt, Yt)
     clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
     if len(want) == 1:
         # profiling runs of a single mode print the timing and stop
@@ -348,7 +455,8 @@ def main():
         Vo = w.potential_at(orc.quad_points(mesh, w.p, w.nq))
         rows = np.sort(np.random.default_rng(1).integers(0, w.num_dofs, 48))
         ridx = torch.from_numpy(rows).cuda()
-        for mode, Xd, Yd in (("fp64", X64, Y64), ("fp32", X32, Y32)):
+        pairs = [("fp64", X64, Y64), ("fp32", X32, Y32)] + [(m,) + ms_tc[m + "_sample"] for m in extra_modes]
+        for mode, Xd, Yd in pairs:
             if Xd is None:
                 continue
             Xr = Xd.double().cpu().numpy()
@@ -360,8 +468,8 @@ def main():
     hbm = peaks["hbm_gbs"]
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     total_units = units * world
-    value = total_units / (ms64 * 1e-3) / 1e9
-    value32 = total_units / (ms32 * 1e-3) / 1e9
+    value = aggregate_throughput(units, ms64, world)
+    value32 = aggregate_throughput(units, ms32, world)
     # dominant kernel: the cell kernel, n_colors launches per step; achieved =
     # algorithmic flops per launch / mean launch duration (event-timed step / launches)
     ach64 = flops / (ms64 * 1e-3) / 1e12
@@ -378,6 +486,12 @@ def main():
                      "hbm_frac": b32 / (ms32 * 1e-3) / 1e9 / hbm,
                      "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x max SM clock"},
     }
+    for m in extra_modes:
+        ach = flops / (ms_tc[m] * 1e-3) / 1e12
+        modes[m] = {"value": total_units / (ms_tc[m] * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_tc[m],
+                    "dtype": "f32 data, %s tensor-core contractions, f32 accumulation" % m,
+                    "rel_err_vs_oracle": acc.get(m), "algorithmic_tflops": ach,
+                    "hbm_frac": b32 / (ms_tc[m] * 1e-3) / 1e9 / hbm}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
@@ -397,6 +511,8 @@ def main():
     }
     if rank == 0 and not args.no_solve:
         out["pcg"] = solve_bench(fe, torch)
+    if rank == 0 and not args.no_batch:
+        out["batch"] = batch_bench(fe, torch)
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

@@ -26,15 +26,17 @@ extern "C" {
 
 /* Training objectives. */
 typedef enum {
-  /* mean over residual snapshots r (columns scaled to norm 1) of (A z(r) - r)^2:
+  /* mean over residual snapshots and columns (r scaled to norm 1) of
+     ||A z(r) - r||^2:
      the network learns to make A z close to r; the gradient runs through the
      operator itself */
   FE_TRAIN_OPERATOR_RESIDUAL = 0,
   /* patch regression onto the oscillatory part of the error (see below) */
   FE_TRAIN_PATCH_ERROR = 1,
-  /* mean over snapshots of (e - z(r))^T A (e - z(r)), e = x* - x_k, both r and
-     e scaled by 1 / ||r|| per column: the energy norm of the error a
-     preconditioned step leaves, the norm CG minimises */
+  /* mean over snapshots and columns of (e - z(r))^T A (e - z(r)), e = x* - x_k,
+     both r and e scaled per column by 1 / ||e||_A = 1 / sqrt(e^T r): the
+     relative energy norm of the error a preconditioned step leaves, the norm
+     CG minimises */
   FE_TRAIN_ENERGY = 2
 } fe_train_objective;
 
@@ -59,7 +61,7 @@ typedef struct {
   float loss_first_epoch;    /* mean MSE over the first epoch */
   float loss_last_epoch;     /* mean MSE over the last epoch */
   double seconds;            /* device time, data generation included */
-  int val_jacobi_iterations; /* FP32 PCG iterations to 1e-6 on the held-out columns, Jacobi */
+  int val_jacobi_iterations; /* FP32 PCG iterations to 1e-7 on the held-out columns, Jacobi */
   int val_learned_iterations;/* the same with the kept checkpoint (the Jacobi count when none beat it) */
   int best_epoch;            /* epoch of the kept checkpoint; 0 = zero output layer (Jacobi) */
 } fe_train_info;
@@ -71,14 +73,15 @@ fe_status fe_precond_init(fe_ctx* ctx, unsigned long long seed);
 /* Train on the residual / error trajectory of an FP32 Jacobi-PCG solve of this
  * operator (n_rhs random right-hand sides, snapshots (r_k, x_k) every
  * snapshot_every iterations, x* = the converged solution), with Adam:
- *  FE_TRAIN_ENERGY: one snapshot per step, loss mean (e_k - z)^T A (e_k - z)
+ *  FE_TRAIN_ENERGY: one snapshot per step, loss mean over columns of
+ *    (e_k - z)^T A (e_k - z)
  *    with z = z(r_k) over all cells' patches at once (one FP32 operator
  *    application per step, which also gives the gradient 2 A (z - e_k));
  *  FE_TRAIN_OPERATOR_RESIDUAL: one snapshot r_k per step, loss
  *    mean (A z(r_k) - r_k)^2 over all cells' patches at once (two FP32
  *    operator applications per step: A z and the gradient A (A z - r));
  *  With n_val > 0 (operator objectives), after every epoch an FP32 block
- *  PCG on n_val held-out random right-hand sides counts iterations to 1e-6
+ *  PCG on n_val held-out random right-hand sides counts iterations to 1e-7
  *  with the current network; the weights of the best epoch are kept, where
  *  "epoch 0" is the network with its output layer set to zero, i.e. exactly
  *  Jacobi -- so the kept network never needs more validation iterations
