@@ -132,6 +132,29 @@ fe_status fe_set_tile(fe_ctx* ctx, fe_mode mode, int vectors_per_cta, int lines,
  * staging memory is kept in the context for reuse. */
 fe_status fe_apply_host(fe_ctx* ctx, const void* X_host, void* Y_host, int n_vec, void* stream);
 
+/* Size of the fixed device staging array of fe_apply_host_noalloc (16 MiB). */
+#define FE_NOALLOC_STAGE_BYTES ((size_t)16 << 20)
+
+/* fe_apply_host for callers that cannot let a library allocate device memory
+ * -- a process whose memory manager reserves the whole GPU up front, a
+ * real-time loop that must never block in the allocator, or an application
+ * held to a fixed, pre-measured memory budget.  (The paper has no
+ * counterpart; it is a deployment variant of fe_apply_host.)  Same contract
+ * as fe_apply_host, but the device staging of X and Y lives in one
+ * file-scope device array of FE_NOALLOC_STAGE_BYTES that every GPU loading
+ * the library holds until the process exits; the call itself performs no
+ * cudaMalloc, cudaFree or other allocation.  Limits and caveats:
+ *  - 2 * num_dofs * n_vec * sizeof(element) (rounded up to 256 bytes for X)
+ *    must fit in FE_NOALLOC_STAGE_BYTES, else FE_EINVAL before any copy;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress with that device current) and caches it; make
+ *    that first call before any stream capture;
+ *  - every call shares the one array: calls that overlap on the GPU (other
+ *    streams, other threads, other contexts on the same device) race and
+ *    must be serialised by the caller.  Nothing in the array needs to start
+ *    at zero: X is copied in whole and Y written whole on every call. */
+fe_status fe_apply_host_noalloc(fe_ctx* ctx, const void* X_host, void* Y_host, int n_vec, void* stream);
+
 /* diag(A) as a device FP64 vector of num_dofs entries (constrained rows get 1,
  * the convention of the Jacobi preconditioner), computed matrix-free from the
  * same tables: A_II = sum over cells containing I of A^(e)_ii. */

@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
         "fe_get_mode": (ctypes.c_int, [_VP]),
         "fe_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
         "fe_apply_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+        "fe_apply_host_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
         "fe_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
         "fe_last_device_status": (ctypes.c_int, [_VP]),
         "fe_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -243,6 +244,20 @@ def fe_apply_host(ctx: int, X, Y, stream=None) -> None:
         return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
     n_vec = X.shape[1]
     _check(lib().fe_apply_host(ctx, ptr(X), ptr(Y), n_vec, _stream_ptr(stream)), "fe_apply_host")
+
+
+NOALLOC_STAGE_BYTES = 16 << 20
+
+
+def fe_apply_host_noalloc(ctx: int, X, Y, stream=None) -> None:
+    """fe_apply_host without any device allocation by the library: the
+    staging lives in a fixed 16 MiB device array (for callers that cannot let
+    a library allocate device memory).  Overlapping calls race."""
+    import torch
+
+    def ptr(a):
+        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+    _check(lib().fe_apply_host_noalloc(ctx, ptr(X), ptr(Y), X.shape[1], _stream_ptr(stream)), "fe_apply_host_noalloc")
 
 
 def fe_diagonal(ctx: int, diag, stream=None) -> None:
