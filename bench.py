@@ -305,9 +305,10 @@ def solve_bench(fe, torch, sub_cols: int = 16):
                               "extrapolated": True}
         out["speedup_mixed_vs_fp64"] = out["fp64_jacobi"]["seconds_extrapolated"] / r["seconds"]
         # learned cell-patch preconditioner: trained on this operator's own Jacobi-PCG
-        # trajectories (16 random right-hand sides, energy-norm objective, checkpoint
-        # picked on 4 held-out right-hand sides), then used inside the mixed solve
-        info = fe.fe_precond_train(ctx, n_rhs=16, snapshots=16, snapshot_every=10, epochs=12, batch=2048, lr=1e-3,
+        # trajectories (8 random right-hand sides, snapshots every 32 iterations,
+        # energy-norm objective, checkpoint picked on 4 held-out right-hand sides),
+        # then used inside the mixed solve
+        info = fe.fe_precond_train(ctx, n_rhs=8, snapshots=16, snapshot_every=32, epochs=6, batch=2048, lr=3e-3,
                                    traj_rtol=1e-6, seed=3, objective="energy", n_val=4)
         X.zero_()
         rl = fe.fe_solve(ctx, Bd, X, rtol=1e-8, max_it=50000, precond="learned", inner_mode="fp32")
@@ -379,6 +380,32 @@ def batch_bench(fe, torch, steps: int = 2):
     return out
 
 
+def profile_precond(fe, torch, n: int = 12, n_vec: int = 128, reps: int = 3):
+    """A small case of the learned-preconditioner inference kernel for
+    hardware-counter captures: n^3 cells, p = 6, n_vec columns, seeded random
+    weights; prints the mean time per application (CUDA events)."""
+    w = inputs.Workload(f"{n}^3 p=6", n, n, n, False, 6, 8, n_vec, "normal", 5, "gauss", v_seed=15, v_amp=0.125,
+                        v_shift=1.0)
+    ctx = fe.setup_workload(w)
+    try:
+        fe.fe_precond_init(ctx, seed=1)
+        R = torch.from_numpy(w.make_rhs()).float().cuda()
+        Z = torch.empty_like(R)
+        fe.fe_precond_apply(ctx, R, Z)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fe.fe_precond_apply(ctx, R, Z)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        print(json.dumps({"workload": w.name, "n_vec": n_vec, "ms_per_precond_apply": ms,
+                          "gflops_mlp": 4 * 128 * (w.p + 1) ** 3 * w.num_cells * n_vec / (ms * 1e-3) / 1e9}))
+    finally:
+        fe.fe_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,6 +417,7 @@ def main():
     ap.add_argument("--modes", default="fp64,fp32")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--profile-precond", type=int, default=0, help="cells per direction of a preconditioner-only run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -403,6 +431,9 @@ def main():
         build.build()
     barrier(world)
     fe.lib()
+    if args.profile_precond:
+        profile_precond(fe, torch, n=args.profile_precond)
+        return
     peaks, peak_src = measured_peaks()
     w = inputs.WORKLOADS[args.workload]
     ctx = fe.setup_workload(w)
