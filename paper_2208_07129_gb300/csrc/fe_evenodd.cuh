@@ -1,0 +1,299 @@
+// Even-odd decomposition of the 1D contractions (FP64 cell kernel).
+//
+// The 1D matrices are (skew-)centrosymmetric: GLL nodes and the quadrature
+// points are symmetric about 0, so N(n_q-1-q, n_p-1-i) = N(q, i) and
+// D~(n_q-1-q, n_q-1-k) = -D~(q, k); folding sqrt(w) keeps both symmetries.
+// For such an M (sign s), out = M in splits into an even and an odd half:
+//   e_i = in_i + in_{n-1-i},  o_i = in_i - in_{n-1-i},
+//   E_q = sum_i (M_qi + M_q,n-1-i)/2 e_i (+ M_q,mid in_mid),
+//   O_q = sum_i (M_qi - M_q,n-1-i)/2 o_i,
+//   out_q = E_q + O_q,   out_{m-1-q} = s (E_q - O_q),
+// about half the multiply-adds of the plain product (the paper's even-odd
+// scheme for its CPU kernels, Sec. 3.2.4; it kept the plain form on V100
+// because of warp stalls -- on GB300 the FP64 pipe is the bound, so the
+// saved FP64 operations are the saved time).  Transposed products use the
+// tables of M^T, which has the same symmetry.
+#pragma once
+
+#include "fe_cell_kernel.cuh"
+
+namespace fe {
+
+// Tables of out = M in for an NO x NI matrix M with M(NO-1-o, NI-1-i) = S M(o, i).
+template <typename T, int NO, int NI>
+struct EOTab {
+  static constexpr int HO = (NO + 1) / 2;   // outputs computed directly
+  static constexpr int HE = (NI + 1) / 2;   // even inputs (with the middle one)
+  static constexpr int HOD = NI / 2 > 0 ? NI / 2 : 1;
+  T E[HO][HE];
+  T O[HO][HOD];
+};
+
+template <typename T, int NP, int NQ>
+struct EOTables {
+  EOTab<T, NQ, NP> N;     // values at points from nodes
+  EOTab<T, NP, NQ> Nt;    // transposed
+  EOTab<T, NQ, NQ> D;     // collocation derivative
+  EOTab<T, NQ, NQ> Dt;    // transposed
+};
+
+template <typename T, int NO, int NI, int S>
+__device__ __forceinline__ void eo_apply(const EOTab<T, NO, NI>& t, const T* in, T* out) {
+  constexpr int HI = NI / 2, HO = (NO + 1) / 2, HE = (NI + 1) / 2;
+  T ie[HE], io[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int i = 0; i < HI; ++i) {
+    ie[i] = in[i] + in[NI - 1 - i];
+    io[i] = in[i] - in[NI - 1 - i];
+  }
+  if (NI & 1) ie[HI] = in[HI];
+#pragma unroll
+  for (int o = 0; o < HO; ++o) {
+    T e = T(0), d = T(0);
+#pragma unroll
+    for (int i = 0; i < HE; ++i) e += t.E[o][i] * ie[i];
+#pragma unroll
+    for (int i = 0; i < HI; ++i) d += t.O[o][i] * io[i];
+    out[o] = e + d;
+    if (o != NO - 1 - o) out[NO - 1 - o] = S > 0 ? e - d : d - e;
+  }
+}
+
+// Same as cell_body (identical data flow, tiles and assembly), with every 1D
+// contraction in even-odd form.
+template <typename T, int NP, int NQ, bool GEN>
+__device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, const MeshDev& m, const Geom<T>& geo,
+                                             int e, int vb, int B, int v, int ty, int nty, int n_vec,
+                                             const T* __restrict__ X, T* __restrict__ Y, T* smem) {
+  constexpr int P = NP - 1;
+  constexpr int NQ3 = NQ * NQ * NQ;
+  T* ST = smem;
+  T* S0 = ST + NQ3 * B;
+  T* S1 = S0 + NQ3 * B;
+  const int vg = vb * B + v;
+  const bool active = vg < n_vec;
+  const int cx = e % m.nx, cy = (e / m.nx) % m.ny, cz = e / (m.nx * m.ny);
+
+  // ---- extraction fused with the x pass of N:  S0[i3][i2][q1] ----
+  for (int l = ty; l < NP * NP; l += nty) {
+    const int i2 = l % NP, i3 = l / NP;
+    const int gy = node_coord(cy, i2, P, m.Ny, m.periodic), gz = node_coord(cz, i3, P, m.Nz, m.periodic);
+    const bool con_yz = on_boundary(gy, m.Ny, m.periodic) || on_boundary(gz, m.Nz, m.periodic);
+    const size_t row = (size_t)(gy + (size_t)m.Ny * gz) * m.Nx;
+    T u[NP], a[NQ];
+#pragma unroll
+    for (int i1 = 0; i1 < NP; ++i1) {
+      const int gx = node_coord(cx, i1, P, m.Nx, m.periodic);
+      const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
+      u[i1] = (active && !con) ? __ldg(X + (row + gx) * n_vec + vg) : T(0);
+    }
+    eo_apply<T, NQ, NP, 1>(tab.N, u, a);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) S0[((i3 * NP + i2) * NQ + q) * B + v] = a[q];
+  }
+  __syncthreads();
+  // ---- y pass of N:  S1[i3][q2][q1] ----
+  for (int l = ty; l < NQ * NP; l += nty) {
+    const int q1 = l % NQ, i3 = l / NQ;
+    T a[NP], b[NQ];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) a[i] = S0[((i3 * NP + i) * NQ + q1) * B + v];
+    eo_apply<T, NQ, NP, 1>(tab.N, a, b);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) S1[((i3 * NQ + q) * NQ + q1) * B + v] = b[q];
+  }
+  __syncthreads();
+  // ---- z pass of N:  ST[q3][q2][q1] ----
+  for (int l = ty; l < NQ * NQ; l += nty) {
+    T a[NP], b[NQ];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) a[i] = S1[(i * NQ * NQ + l) * B + v];
+    eo_apply<T, NQ, NP, 1>(tab.N, a, b);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) ST[(q * NQ * NQ + l) * B + v] = b[q];
+  }
+  __syncthreads();
+  // ---- reference gradients along x (-> S0) and y (-> S1) ----
+  for (int l = ty; l < 2 * NQ * NQ; l += nty) {
+    const bool ydir = l >= NQ * NQ;
+    const int ll = ydir ? l - NQ * NQ : l;
+    const int base = ydir ? (ll % NQ) + (ll / NQ) * NQ * NQ : ll * NQ;
+    const int stride = ydir ? NQ : 1;
+    T t[NQ], g[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) t[k] = ST[(base + k * stride) * B + v];
+    eo_apply<T, NQ, NQ, -1>(tab.D, t, g);
+    T* dst = ydir ? S1 : S0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dst[(base + q * stride) * B + v] = g[q];
+  }
+  __syncthreads();
+  // ---- z-lines: gradient along z, quadrature-point operation, transposed z pass ----
+  T g00, g01, g02, g11, g12, g22;
+  if (!GEN) {
+    g00 = geo.cellG[e * 6 + 0]; g01 = geo.cellG[e * 6 + 1]; g02 = geo.cellG[e * 6 + 2];
+    g11 = geo.cellG[e * 6 + 3]; g12 = geo.cellG[e * 6 + 4]; g22 = geo.cellG[e * 6 + 5];
+  }
+  const T* ptC = geo.ptC + (size_t)e * NQ3;
+  for (int l = ty; l < NQ * NQ; l += nty) {
+    T t[NQ], h2[NQ], o[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) t[k] = ST[(k * NQ * NQ + l) * B + v];
+    eo_apply<T, NQ, NQ, -1>(tab.D, t, h2);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const T d2 = h2[q];
+      const int Q = q * NQ * NQ + l;
+      const T d0 = S0[Q * B + v], d1 = S1[Q * B + v];
+      if (GEN) {
+        const T* pg = geo.ptG + (size_t)e * 6 * NQ3 + Q;
+        g00 = pg[0]; g01 = pg[NQ3]; g02 = pg[2 * NQ3]; g11 = pg[3 * NQ3]; g12 = pg[4 * NQ3]; g22 = pg[5 * NQ3];
+      }
+      S0[Q * B + v] = g00 * d0 + g01 * d1 + g02 * d2;
+      S1[Q * B + v] = g01 * d0 + g11 * d1 + g12 * d2;
+      h2[q] = g02 * d0 + g12 * d1 + g22 * d2;
+      t[q] = ptC[Q] * t[q];
+    }
+    eo_apply<T, NQ, NQ, -1>(tab.Dt, h2, o);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) ST[(k * NQ * NQ + l) * B + v] = t[k] + o[k];
+  }
+  __syncthreads();
+  // ---- transposed x pass of D~ accumulated into T ----
+  for (int l = ty; l < NQ * NQ; l += nty) {
+    const int base = l * NQ;
+    T h[NQ], o[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) h[q] = S0[(base + q) * B + v];
+    eo_apply<T, NQ, NQ, -1>(tab.Dt, h, o);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) ST[(base + k) * B + v] += o[k];
+  }
+  __syncthreads();
+  // ---- transposed y pass of D~ accumulated into T ----
+  for (int l = ty; l < NQ * NQ; l += nty) {
+    const int base = (l % NQ) + (l / NQ) * NQ * NQ;
+    T h[NQ], o[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) h[q] = S1[(base + q * NQ) * B + v];
+    eo_apply<T, NQ, NQ, -1>(tab.Dt, h, o);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) ST[(base + k * NQ) * B + v] += o[k];
+  }
+  __syncthreads();
+  // ---- transposed z pass of N:  S1[i3][q2][q1] ----
+  for (int l = ty; l < NQ * NQ; l += nty) {
+    T t[NQ], o[NP];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) t[q] = ST[(q * NQ * NQ + l) * B + v];
+    eo_apply<T, NP, NQ, 1>(tab.Nt, t, o);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) S1[(i * NQ * NQ + l) * B + v] = o[i];
+  }
+  __syncthreads();
+  // ---- transposed y pass of N:  S0[i3][i2][q1] ----
+  for (int l = ty; l < NQ * NP; l += nty) {
+    const int q1 = l % NQ, i3 = l / NQ;
+    T t[NQ], o[NP];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) t[q] = S1[((i3 * NQ + q) * NQ + q1) * B + v];
+    eo_apply<T, NP, NQ, 1>(tab.Nt, t, o);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) S0[((i3 * NP + i) * NQ + q1) * B + v] = o[i];
+  }
+  __syncthreads();
+  // ---- transposed x pass of N fused with assembly ----
+  for (int l = ty; l < NP * NP; l += nty) {
+    const int i2 = l % NP, i3 = l / NP;
+    T t[NQ], o[NP];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) t[q] = S0[((i3 * NP + i2) * NQ + q) * B + v];
+    if (!active) continue;
+    eo_apply<T, NP, NQ, 1>(tab.Nt, t, o);
+    const int gy = node_coord(cy, i2, P, m.Ny, m.periodic), gz = node_coord(cz, i3, P, m.Nz, m.periodic);
+    const bool con_yz = on_boundary(gy, m.Ny, m.periodic) || on_boundary(gz, m.Nz, m.periodic);
+    const bool first_yz = first_along(cy, m.ny, i2, P, m.periodic, m.last_odd_y) &&
+                          first_along(cz, m.nz, i3, P, m.periodic, m.last_odd_z);
+    const size_t row = (size_t)(gy + (size_t)m.Ny * gz) * m.Nx;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const int gx = node_coord(cx, i, P, m.Nx, m.periodic);
+      const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
+      const bool first = first_yz && first_along(cx, m.nx, i, P, m.periodic, m.last_odd_x);
+      T* dst = Y + (row + gx) * n_vec + vg;
+      if (first) *dst = con ? T(0) : o[i];
+      else if (!con) *dst += o[i];
+    }
+  }
+}
+
+template <typename T, int NP, int NQ, bool GEN>
+__global__ void __launch_bounds__(256) cell_apply_eo_kernel(const EOTables<T, NP, NQ> tab, const MeshDev m,
+                                                            const Geom<T> geo, const int* __restrict__ cells,
+                                                            int n_vec, int n_vb, const T* __restrict__ X,
+                                                            T* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cell_body_eo<T, NP, NQ, GEN>(tab, m, geo, cells[blockIdx.x / n_vb], blockIdx.x % n_vb, blockDim.x, threadIdx.x,
+                               threadIdx.y, blockDim.y, n_vec, X, Y, reinterpret_cast<T*>(smem_raw));
+}
+
+// Host: even-odd tables of an NO x NI row-major matrix M with symmetry S.
+template <typename T, int NO, int NI>
+void make_eotab(EOTab<T, NO, NI>& t, const double* M) {
+  constexpr int HI = NI / 2, HO = (NO + 1) / 2, HE = (NI + 1) / 2;
+  for (int o = 0; o < HO; ++o) {
+    for (int i = 0; i < HI; ++i) {
+      t.E[o][i] = (T)(0.5 * (M[o * NI + i] + M[o * NI + NI - 1 - i]));
+      t.O[o][i] = (T)(0.5 * (M[o * NI + i] - M[o * NI + NI - 1 - i]));
+    }
+    if (HE > HI) t.E[o][HI] = (T)M[o * NI + HI];
+  }
+}
+
+template <typename T, int NP, int NQ>
+EOTables<T, NP, NQ> make_eotables(const fe_ctx* c) {
+  EOTables<T, NP, NQ> t;
+  double Nt[NP * NQ], Dt[NQ * NQ];
+  for (int q = 0; q < NQ; ++q) {
+    for (int i = 0; i < NP; ++i) Nt[i * NQ + q] = c->Nf[q * NP + i];
+    for (int k = 0; k < NQ; ++k) Dt[k * NQ + q] = c->Df[q * NQ + k];
+  }
+  make_eotab<T, NQ, NP>(t.N, c->Nf.data());
+  make_eotab<T, NP, NQ>(t.Nt, Nt);
+  make_eotab<T, NQ, NQ>(t.D, c->Df.data());
+  make_eotab<T, NQ, NQ>(t.Dt, Dt);
+  return t;
+}
+
+template <typename T, int NP, int NQ, bool GEN>
+cudaError_t launch_apply_eo(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaStream_t s, int want_vb,
+                            int want_lines) {
+  auto kern = cell_apply_eo_kernel<T, NP, NQ, GEN>;
+  const int vb = pick_vb<T, NQ>(want_vb, n_vec);
+  int nty = want_lines;
+  if (vb * nty > 256) nty = 256 / vb;
+  while ((vb * nty) % 32 != 0 && vb * nty < 256) ++nty;
+  const size_t smem = (size_t)3 * NQ * NQ * NQ * vb * sizeof(T);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  const EOTables<T, NP, NQ> tab = make_eotables<T, NP, NQ>(c);
+  const Geom<T> geo = make_geom<T>(c);
+  const int n_vb = (n_vec + vb - 1) / vb;
+  for (int k = 0; k < c->colors.n_colors; ++k) {
+    const int n = c->colors.offset[k + 1] - c->colors.offset[k];
+    if (n == 0) continue;
+    const long long blocks = (long long)n * n_vb;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<(unsigned)blocks, dim3(vb, nty), smem, s>>>(tab, c->mdev, geo, c->d_cells + c->colors.offset[k], n_vec,
+                                                       n_vb, X, Y);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace fe

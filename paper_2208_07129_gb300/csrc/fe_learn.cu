@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_precond_kernel(const MlpAr
   uint64_t* mbar = reinterpret_cast<uint64_t*>(reg2 + kTile * kHidden * 2);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   float* ssq = reinterpret_cast<float*>(tslot + 4);   // [2][128] partial squared norms
+  long long* noff = reinterpret_cast<long long*>(ssq + 2 * kTile);   // per node: global DoF, -1 if constrained
+  float* nw = reinterpret_cast<float*>(noff + a.K1);                // per node: partition-of-unity weight
 
   const int t = threadIdx.x, warp = t >> 5;
   const int row = t & (kTile - 1), half = t >> 7;
@@ -182,29 +184,39 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_precond_kernel(const MlpAr
   }
   if (t == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
 
+  // the cell's node offsets and weights, once per CTA
+  for (int i = t; i < a.K1; i += kMlpThreads) {
+    long long off = -1;
+    float wgt = 0.f;
+    if (i < a.n3) {
+      size_t dof;
+      bool con;
+      node_info(m, P, a.np, cx, cy, cz, i, &dof, &con, &wgt);
+      off = con ? -1 : (long long)dof;
+    }
+    noff[i] = off;
+    nw[i] = wgt;
+  }
   // W1 image -> shared (straight 16-byte copy)
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.W1img);
     uint4* dst = reinterpret_cast<uint4*>(reg1);
+#pragma unroll 4
     for (size_t k = t; k < img / 16; k += kMlpThreads) dst[k] = __ldg(src + k);
   }
+  __syncthreads();
   // gather the patch of column `col` (row `row` of the tile), 8 nodes per 16-byte chunk
   float ss = 0.f;
+#pragma unroll 2
   for (int kg = half; kg < a.K1 / 8; kg += 2) {
     float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int i = kg * 8 + u;
-      v[u] = 0.f;
-      if (active && i < a.n3) {
-        size_t dof;
-        bool con;
-        float w;
-        node_info(m, P, a.np, cx, cy, cz, i, &dof, &con, &w);
-        if (!con) v[u] = __ldg(R + dof * n_vec + col);
-      }
-      ss += v[u] * v[u];
+      const long long off = noff[kg * 8 + u];
+      v[u] = (active && off >= 0) ? __ldg(R + off * n_vec + col) : 0.f;
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) ss += v[u] * v[u];
     uint4 chunk;
     chunk.x = pack_bf16(v[0], v[1]);
     chunk.y = pack_bf16(v[2], v[3]);
@@ -242,6 +254,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_precond_kernel(const MlpAr
     // the patch tile is consumed: bring the W2 image into its place
     const uint4* src = reinterpret_cast<const uint4*>(a.W2img);
     uint4* dst = reinterpret_cast<uint4*>(reg0);
+#pragma unroll 4
     for (size_t k = t; k < img / 16; k += kMlpThreads) dst[k] = __ldg(src + k);
     // h = relu(D1 / s + b1) -> BF16 hidden tile, row `row`, columns of this half
     for (int c0 = half * 32; c0 < kHidden; c0 += 64) {
@@ -287,15 +300,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_precond_kernel(const MlpAr
       float d[32];
       tmem_ld32(lane_base + kHidden + c0, d);
       if (!active) continue;
-#pragma unroll 8
+#pragma unroll
       for (int u = 0; u < 32; ++u) {
         const int i = c0 + u;
-        if (i >= a.n3) break;
-        size_t dof;
-        bool con;
-        float w;
-        node_info(m, P, a.np, cx, cy, cz, i, &dof, &con, &w);
-        if (!con) Z[dof * n_vec + col] += (d[u] + __ldg(a.b2 + i)) * s * w;
+        const long long off = i < a.n3 ? noff[i] : -1;
+        if (off >= 0) Z[off * n_vec + col] += (d[u] + __ldg(a.b2 + i)) * s * nw[i];
       }
     }
   } else if (t == 0) {
@@ -715,7 +724,9 @@ static fe_status from_cuda(cudaError_t e) {
   return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
 }
 
-static size_t smem_bytes(int K1) { return (size_t)2 * kTile * K1 * 2 + kTile * kHidden * 2 + 32 + 2 * kTile * 4; }
+static size_t smem_bytes(int K1) {
+  return (size_t)2 * kTile * K1 * 2 + kTile * kHidden * 2 + 32 + 2 * kTile * 4 + (size_t)K1 * 12;
+}
 
 static cudaError_t alloc_learned(fe_ctx* c) {
   if (c->learned) return cudaSuccess;

@@ -201,6 +201,8 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
   c->periodic = mesh->bc == FE_BC_PERIODIC;
   c->p = p; c->np = p + 1; c->nq = quad->n_q; c->quad_kind = quad->kind; c->mu = mu;
   c->general = mesh->vertex_xyz != nullptr;
+  // FP64 tile measured on GB300: 8 vectors x 16 lines up to n_q = 8, 4 x 32 above
+  if (quad->n_q >= 9) { c->vb64 = 4; c->nty64 = 32; }
   const int np = c->np, nq = c->nq;
   const int add = c->periodic ? 0 : 1;
   c->mdev.nx = c->nx; c->mdev.ny = c->ny; c->mdev.nz = c->nz;
@@ -385,6 +387,7 @@ extern "C" fe_status fe_set_tile(fe_ctx* c, fe_mode mode, int vectors_per_cta, i
     if (variant == 2) return FE_EINVAL;
     c->vb64 = vectors_per_cta;
     c->nty64 = lines;
+    c->fp64_variant = variant;
   } else if (mode == FE_FP32) {
     if (variant == 2 && c->nq > 8) return FE_EUNSUPPORTED;
     c->vb32 = vectors_per_cta;

@@ -39,6 +39,8 @@ def test_batch_matches_per_problem(fe, mode, autotune):
             Xs.append(X)
             Ys.append(torch.full_like(X, float("nan")))
             fe.fe_set_mode(ctx, mode)
+            if mode == "fp64":
+                fe.fe_set_tile(ctx, "fp64", 8, 16, 1)   # the plain line kernel, whose cell body the batch runs
             Y = torch.empty_like(X)
             fe.fe_apply(ctx, X, Y)
             Yref.append(Y)
