@@ -51,11 +51,26 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// A 3D tile [e2][e1][e0] x 16 vectors in shared memory.
+// A 3D tile [e2][e1][e0] x 16 vectors in shared memory.  With an even e0 <= 8
+// (measured: at e0 = 10 the extra index arithmetic costs more than the
+// conflicts it removes) the tile is swizzled so that the four entries k of an MMA operand fragment,
+// which lie on one line along x, y or z, fall into four different bank groups:
+// element slot = elem ^ ((y + z) & 1) (this swaps x and x ^ 1 inside a row, so
+// the slot's parity is (x + y + z) & 1 and selects the 16-word half of a
+// 32-bank row) and the vector index is XORed with 8 ((x/2 + y/2 + z/2) & 1)
+// (the 8-word half inside it).  Four consecutive positions along any axis have
+// distinct (c & 1, (c >> 1) & 1), hence distinct bank groups.
 struct Tile {
   float* p;
   int e0, e1, e2;
-  __device__ __forceinline__ float& at(int x, int y, int z, int v) const { return p[((z * e1 + y) * e0 + x) * 16 + v]; }
+  __device__ __forceinline__ float& at(int x, int y, int z, int v) const {
+    int elem = (z * e1 + y) * e0 + x;
+    if (!(e0 & 1) && e0 <= 8) {
+      elem ^= (y + z) & 1;
+      v ^= (((x >> 1) + (y >> 1) + (z >> 1)) & 1) << 3;
+    }
+    return p[elem * 16 + v];
+  }
 };
 
 // Coordinates of entry k of line `line` along axis `ax` of a tile with extents (e0, e1, e2).
