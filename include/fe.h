@@ -128,10 +128,17 @@ fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream)
  * later fe_apply calls. */
 fe_status fe_set_tile(fe_ctx* ctx, fe_mode mode, int vectors_per_cta, int lines, int variant);
 
-/* Same product with HOST buffers: copies X_host to library-owned device
- * staging memory, applies, copies the result to Y_host and synchronises the
- * stream.  For pinned host buffers the copies are asynchronous DMA.  The
- * staging memory is kept in the context for reuse. */
+/* Same product with HOST buffers (num_dofs x n_vec, DoF-major, in the
+ * context's element type): copies X_host to library-owned device staging
+ * memory, applies, copies the result to Y_host and synchronises `stream`
+ * before returning.  A block of at least two 128-byte column chunks (32 FP64
+ * or 64 FP32 vectors) is pipelined: chunks of 16 (FP64) or 32 (FP32) columns
+ * are copied in and out by strided copies on two library-owned streams while
+ * the previous chunk is applied on `stream`, so the link transfers hide under
+ * the product; each column's result is bitwise that of fe_apply on the whole
+ * block.  Pinned host buffers give asynchronous DMA.  The staging memory (4
+ * chunks, or X and Y for a narrow block), the streams and the events stay in
+ * the context for reuse; concurrent calls on one context race. */
 fe_status fe_apply_host(fe_ctx* ctx, const void* X_host, void* Y_host, int n_vec, void* stream);
 
 /* Size of the fixed device staging array of fe_apply_host_noalloc (16 MiB). */

@@ -101,9 +101,12 @@ struct fe_ctx {
   float *d_cellG32 = nullptr, *d_ptG32 = nullptr, *d_ptC32 = nullptr;
   double* d_detJ = nullptr;
   int* d_status = nullptr;
-  // staging for fe_apply_host
+  // staging for fe_apply_host, and the copy streams and events of its
+  // pipeline (created on first use)
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
   fe_mode mode = FE_FP64;
   fe_mode inner_mode = FE_FP32;   // arithmetic of the inner solve (refinement)
   fe::SolveWs ws;

@@ -317,6 +317,10 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->d_cells); cudaFree(c->d_cellG64); cudaFree(c->d_ptG64); cudaFree(c->d_ptC64);
   cudaFree(c->d_cellG32); cudaFree(c->d_ptG32); cudaFree(c->d_ptC32); cudaFree(c->d_detJ);
   cudaFree(c->d_status); cudaFree(c->d_stage);
+  if (c->copy_in) cudaStreamDestroy(c->copy_in);
+  if (c->copy_out) cudaStreamDestroy(c->copy_out);
+  for (cudaEvent_t ev : {c->ev_start, c->ev_in[0], c->ev_in[1], c->ev_comp[0], c->ev_comp[1], c->ev_out[0], c->ev_out[1]})
+    if (ev) cudaEventDestroy(ev);
   free_solver_workspace(c);
   free_learned(c);
   delete c;

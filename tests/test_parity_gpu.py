@@ -156,6 +156,31 @@ def test_host_buffer_apply(fe):
         fe.fe_destroy(ctx)
 
 
+@pytest.mark.parametrize("mode,n_vec", [("fp64", 37), ("fp32", 70), ("tf32", 64)])
+def test_host_buffer_apply_pipelined(fe, mode, n_vec):
+    """Blocks of at least two 128-byte chunks go through the copy/compute
+    pipeline (ragged last chunk here); every column must equal the device
+    product of the whole block bit for bit."""
+    ctx, mesh, Vo = _setup_pair(fe, 3, 2, 3, 4, 6)
+    try:
+        fe.fe_set_mode(ctx, mode)
+        dt = torch.float64 if mode == "fp64" else torch.float32
+        X = torch.from_numpy(inputs.random_block(fe.fe_num_dofs(ctx), n_vec, "uniform", 5)).to(dt)
+        Xh = X.pin_memory()
+        Yh = torch.full_like(Xh, float("nan")).pin_memory()
+        for _ in range(2):            # second call reuses the stage and the streams
+            fe.fe_apply_host(ctx, Xh, Yh)
+        Xd = X.cuda()
+        Yd = torch.empty_like(Xd)
+        fe.fe_apply(ctx, Xd, Yd)
+        torch.cuda.synchronize()
+        assert torch.equal(Yh, Yd.cpu())
+        if mode == "fp64":
+            _compare(Yh.numpy(), orc.apply(mesh, 4, 6, X.numpy(), Vq=Vo), FP64_TOL)
+    finally:
+        fe.fe_destroy(ctx)
+
+
 def test_diagonal(fe):
     verts = inputs.perturbed_vertices(2, 2, 3, seed=8)
     for periodic, v in ((True, None), (False, verts)):
