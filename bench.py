@@ -338,7 +338,7 @@ def distorted_bench(fe, torch, steps: int = 2, rows: int = 24):
         Vo = w.potential_at(orc.quad_points(mesh, w.p, w.nq))
         ridx = np.sort(np.random.default_rng(3).integers(0, w.num_dofs, rows))
         rt = torch.from_numpy(ridx).cuda()
-        for mode in ("fp64", "fp32", "tf32", "bf16"):
+        for mode in ("fp64", "fp32", "tf32", "bf16", "tf32x3"):
             fe.fe_set_mode(ctx, mode)
             dt = torch.float64 if mode == "fp64" else torch.float32
             X = torch.from_numpy(X64).to(device="cuda", dtype=dt)
@@ -488,7 +488,7 @@ def main():
 
     modes = {}
     want = args.modes.split(",")
-    extra_modes = [m for m in ("tf32", "bf16") if m in want or args.modes == "fp64,fp32"]
+    extra_modes = [m for m in ("tf32", "bf16", "tf32x3") if m in want or args.modes == "fp64,fp32"]
     with ClockSampler(local) as clk:
         ms64 = ms32 = float("nan")
         X64 = Y64 = X32 = Y32 = None
@@ -564,7 +564,8 @@ def main():
     for m in extra_modes:
         ach = flops / (ms_tc[m] * 1e-3) / 1e12
         modes[m] = {"value": total_units / (ms_tc[m] * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_tc[m],
-                    "dtype": "f32 data, %s tensor-core contractions, f32 accumulation" % m,
+                    "dtype": "f32 data, %s tensor-core contractions, f32 accumulation"
+                             % ("split-TF32 (hi+lo, 3 products)" if m == "tf32x3" else m),
                     "rel_err_vs_oracle": acc.get(m), "algorithmic_tflops": ach,
                     "hbm_frac": b32 / (ms_tc[m] * 1e-3) / 1e9 / hbm}
     out = {

@@ -60,8 +60,12 @@ typedef enum { FE_QUAD_GAUSS = 0, FE_QUAD_GLL = 1 } fe_quad_kind;
  * FE_FP32: float data, float arithmetic on CUDA cores.  FE_TF32 / FE_BF16:
  * float data, the sum-factorised contractions on tensor cores with FP32
  * accumulation (operands rounded to TF32 / BF16); the quadrature-point
- * operation stays FP32.  Geometry is always computed in FP64. */
-typedef enum { FE_FP64 = 0, FE_FP32 = 1, FE_TF32 = 2, FE_BF16 = 3 } fe_mode;
+ * operation stays FP32.  FE_TF32X3: as FE_TF32, but every operand is split
+ * into hi + lo TF32 parts and each product is accumulated as
+ * lo*hi + hi*lo + hi*hi (three tensor-core products; the split-TF32 scheme of
+ * Ootomo and Yokota, 2022), which restores FP32-level accuracy.  Geometry is
+ * always computed in FP64. */
+typedef enum { FE_FP64 = 0, FE_FP32 = 1, FE_TF32 = 2, FE_BF16 = 3, FE_TF32X3 = 4 } fe_mode;
 
 typedef struct {
   int nx, ny, nz;          /* cells per direction, >= 1 (>= 2 when periodic) */
@@ -190,7 +194,7 @@ typedef struct {
  * X's boundary rows stay 0.
  *   inner_mode == FE_FP64: PCG in FP64.
  *   otherwise: FP64 iterative refinement -- r = B - A X with the FP64
- *   operator, an inner PCG in inner_mode (FP32 data; FE_FP32/TF32/BF16
+ *   operator, an inner PCG in inner_mode (FP32 data; FE_FP32/TF32/BF16/TF32X3
  *   operator) on r / ||r|| to the relative reduction still needed
  *   (rtol ||b|| / (2 ||r||), at least 2e-6), X += ||r|| D -- until every
  *   column reaches rtol.

@@ -31,8 +31,9 @@ extern "C" fe_status fe_apply(fe_ctx* c, const void* X, void* Y, int n_vec, void
     case FE_FP32: e = apply_cc_f32(c, static_cast<const float*>(X), static_cast<float*>(Y), n_vec, s); break;
     case FE_TF32:
     case FE_BF16:
+    case FE_TF32X3:
       if ((size_t)3 * c->nq * c->nq * c->nq * 16 * sizeof(float) > 220 * 1024) return FE_EUNSUPPORTED;
-      e = apply_mma_f32(c, static_cast<const float*>(X), static_cast<float*>(Y), n_vec, s, c->mode == FE_BF16);
+      e = apply_mma_f32(c, static_cast<const float*>(X), static_cast<float*>(Y), n_vec, s, c->mode);
       break;
     default: return FE_EUNSUPPORTED;
   }

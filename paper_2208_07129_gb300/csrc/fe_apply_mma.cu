@@ -1,21 +1,20 @@
-// Tensor-core (TF32 / BF16 warp MMA) instantiations of the cell kernel.
-#include "fe_dispatch.cuh"
-#include "fe_mma_kernel.cuh"
+// Tensor-core cell kernels: mode dispatch.  Each operand kind is compiled in
+// its own translation unit (fe_apply_mma_<kind>.cu) so that the build runs
+// them in parallel.
+#include "fe_internal.h"
 
 namespace fe {
 
-cudaError_t apply_mma_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s, bool bf16) {
-#define FE_CASE(P, NQ)                                                                        \
-  if (c->p == P && c->nq == NQ) {                                                             \
-    if (c->general)                                                                           \
-      return bf16 ? launch_mma<P + 1, NQ, true, true>(c, X, Y, n_vec, s)                     \
-                  : launch_mma<P + 1, NQ, true, false>(c, X, Y, n_vec, s);                   \
-    return bf16 ? launch_mma<P + 1, NQ, false, true>(c, X, Y, n_vec, s)                      \
-                : launch_mma<P + 1, NQ, false, false>(c, X, Y, n_vec, s);                    \
+template <int KIND>
+cudaError_t apply_mma_kind(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);
+
+cudaError_t apply_mma_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s, fe_mode mode) {
+  switch (mode) {
+    case FE_TF32: return apply_mma_kind<0>(c, X, Y, n_vec, s);
+    case FE_BF16: return apply_mma_kind<1>(c, X, Y, n_vec, s);
+    case FE_TF32X3: return apply_mma_kind<2>(c, X, Y, n_vec, s);
+    default: return cudaErrorInvalidValue;
   }
-  FE_FOR_EACH_P_NQ(FE_CASE)
-#undef FE_CASE
-  return cudaErrorInvalidValue;
 }
 
 }  // namespace fe

@@ -122,7 +122,7 @@ namespace fe {
 cudaError_t apply_cc_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s);
 cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);
 cudaError_t diagonal_f64(const fe_ctx* c, double* diag, cudaStream_t s);
-cudaError_t apply_mma_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s, bool bf16);
+cudaError_t apply_mma_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s, fe_mode mode);
 // Solver workspace and the learned preconditioner (fe_solve.cu / fe_learn.cu).
 cudaError_t solver_workspace(fe_ctx* c, int nv);
 void free_solver_workspace(fe_ctx* c);

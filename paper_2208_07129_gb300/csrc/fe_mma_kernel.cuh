@@ -11,8 +11,12 @@
 // quadrature-point operation is applied to the accumulator fragments of the
 // z-gradient pass, whose transposed z pass takes c T as its accumulator input.
 // Operands are rounded to TF32 (cvt.rna) or BF16 (round to nearest even);
-// every sum is accumulated in FP32.  Assembly: colour-ordered, first writer
-// stores, as in the CUDA-core kernels.
+// every sum is accumulated in FP32.  The split-TF32 kind (3xTF32) writes
+// every operand as hi + lo, both TF32, and accumulates lo*hi + hi*lo + hi*hi:
+// three MMAs per product, with only the lo*lo term (relative size 2^-22)
+// dropped, which gives FP32-level accuracy on the tensor cores (the
+// error-free splitting of Ootomo and Yokota, 2022).  Assembly: colour-ordered,
+// first writer stores, as in the CUDA-core kernels.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -23,6 +27,22 @@ namespace fe {
 
 constexpr int kMmaVB = 16;   // vectors per CTA (the MMA's M)
 constexpr int kMmaWarps = 8;
+
+// Operand kinds of the tensor-core kernel.
+constexpr int kTF32 = 0, kBF16 = 1, kTF32x3 = 2;
+
+// x rounded to the nearest TF32 value (10 explicit mantissa bits; ties away
+// from zero), as an FP32 bit pattern with the 13 low bits clear.  Used for the
+// hi/lo split, where both parts must be exact TF32 values.
+__device__ __forceinline__ uint32_t tf32_round_bits(float x) {
+  return (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+}
+
+// x = hi + lo + O(2^-22 |x|), hi and lo both TF32.
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_round_bits(x);
+  lo = tf32_round_bits(x - __uint_as_float(hi));
+}
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -82,30 +102,39 @@ __device__ __forceinline__ void line_coord(int ax, int line, int k, int e0, int 
 
 // Matrix fragments of one pass: M(k, n) for k < KIN, n < NOUT, as B operands
 // of the MMA (col layout), for every (k-step, n-tile).
-template <bool BF16, int KIN, int NOUT>
+template <int KIND, int KIN, int NOUT>
 struct BFrags {
+  static constexpr bool BF16 = KIND == kBF16;
   static constexpr int KS = BF16 ? (KIN + 15) / 16 : (KIN + 7) / 8;   // k-steps
   static constexpr int NT = (NOUT + 7) / 8;                           // n-tiles
+  static constexpr int KSL = KIND == kTF32x3 ? KS : 1;                // lo parts (split kind only)
+  static constexpr int NTL = KIND == kTF32x3 ? NT : 1;
   uint32_t b[KS][NT][2];
+  uint32_t bl[KSL][NTL][2];
 };
 
 // M(k, n) = tab[n][k] (forward: rows of N or D~ are outputs) or tab[k][n] (transposed).
-template <bool BF16, int KIN, int NOUT, int R, int C>
-__device__ __forceinline__ void load_bfrags(BFrags<BF16, KIN, NOUT>& f, const float (&tab)[R][C], bool trans) {
+template <int KIND, int KIN, int NOUT, int R, int C>
+__device__ __forceinline__ void load_bfrags(BFrags<KIND, KIN, NOUT>& f, const float (&tab)[R][C], bool trans) {
+  constexpr bool BF16 = KIND == kBF16;
   const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
   auto M = [&](int k, int n) -> float {
     if (k >= KIN || n >= NOUT) return 0.f;
     return trans ? tab[k][n] : tab[n][k];
   };
 #pragma unroll
-  for (int ks = 0; ks < BFrags<BF16, KIN, NOUT>::KS; ++ks)
+  for (int ks = 0; ks < BFrags<KIND, KIN, NOUT>::KS; ++ks)
 #pragma unroll
-    for (int nt = 0; nt < BFrags<BF16, KIN, NOUT>::NT; ++nt) {
+    for (int nt = 0; nt < BFrags<KIND, KIN, NOUT>::NT; ++nt) {
       const int n = nt * 8 + g;
       if (BF16) {
         const int k0 = ks * 16 + 2 * t4;
         f.b[ks][nt][0] = pack_bf16x2(M(k0, n), M(k0 + 1, n));
         f.b[ks][nt][1] = pack_bf16x2(M(k0 + 8, n), M(k0 + 9, n));
+      } else if (KIND == kTF32x3) {
+        const int k0 = ks * 8 + t4;
+        split_tf32(M(k0, n), f.b[ks][nt][0], f.bl[ks % f.KSL][nt % f.NTL][0]);
+        split_tf32(M(k0 + 4, n), f.b[ks][nt][1], f.bl[ks % f.KSL][nt % f.NTL][1]);
       } else {
         const int k0 = ks * 8 + t4;
         f.b[ks][nt][0] = to_tf32(M(k0, n));
@@ -122,14 +151,32 @@ struct DFrag {
 };
 
 // A-operand loader: a(v, k) for the 16 vectors.  `get(v, k)` returns the FP32 value.
-template <bool BF16, int KIN, int NOUT, typename Get>
-__device__ __forceinline__ void line_mma(const BFrags<BF16, KIN, NOUT>& f, DFrag<BFrags<BF16, KIN, NOUT>::NT>& acc,
+template <int KIND, int KIN, int NOUT, typename Get>
+__device__ __forceinline__ void line_mma(const BFrags<KIND, KIN, NOUT>& f, DFrag<BFrags<KIND, KIN, NOUT>::NT>& acc,
                                          Get get) {
+  constexpr bool BF16 = KIND == kBF16;
   const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-  constexpr int KS = BFrags<BF16, KIN, NOUT>::KS, NT = BFrags<BF16, KIN, NOUT>::NT;
+  constexpr int KS = BFrags<KIND, KIN, NOUT>::KS, NT = BFrags<KIND, KIN, NOUT>::NT;
 #pragma unroll
   for (int ks = 0; ks < KS; ++ks) {
     uint32_t a[4];
+    if (KIND == kTF32x3) {
+      const int k0 = ks * 8 + t4;
+      auto v = [&](int vv, int k) { return k < KIN ? get(vv, k) : 0.f; };
+      uint32_t al[4];
+      split_tf32(v(g, k0), a[0], al[0]);
+      split_tf32(v(g + 8, k0), a[1], al[1]);
+      split_tf32(v(g, k0 + 4), a[2], al[2]);
+      split_tf32(v(g + 8, k0 + 4), a[3], al[3]);
+      // small terms first
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        mma_tf32(acc.d[nt], al, f.b[ks][nt]);
+        mma_tf32(acc.d[nt], a, f.bl[ks % f.KSL][nt % f.NTL]);
+        mma_tf32(acc.d[nt], a, f.b[ks][nt]);
+      }
+      continue;
+    }
     if (BF16) {
       const int k0 = ks * 16 + 2 * t4;
       auto v = [&](int vv, int k) { return k < KIN ? get(vv, k) : 0.f; };
@@ -167,10 +214,10 @@ __device__ __forceinline__ void for_frag(DFrag<NT>& acc, F fn) {
 }
 
 // One pass over all lines along axis `ax`: dst(line, n) (+)= sum_k src(line, k) M(k, n).
-template <bool BF16, int KIN, int NOUT, bool ACC>
-__device__ __forceinline__ void pass(const BFrags<BF16, KIN, NOUT>& f, const Tile& src, const Tile& dst, int ax,
+template <int KIND, int KIN, int NOUT, bool ACC>
+__device__ __forceinline__ void pass(const BFrags<KIND, KIN, NOUT>& f, const Tile& src, const Tile& dst, int ax,
                                      int n_lines) {
-  constexpr int NT = BFrags<BF16, KIN, NOUT>::NT;
+  constexpr int NT = BFrags<KIND, KIN, NOUT>::NT;
   const int warp = threadIdx.x >> 5;
   for (int line = warp; line < n_lines; line += kMmaWarps) {
     DFrag<NT> acc;
@@ -183,7 +230,7 @@ __device__ __forceinline__ void pass(const BFrags<BF16, KIN, NOUT>& f, const Til
         x = dst.at(a, b, c, v);
       });
     }
-    line_mma<BF16, KIN, NOUT>(f, acc, [&](int v, int k) {
+    line_mma<KIND, KIN, NOUT>(f, acc, [&](int v, int k) {
       int a, b, c;
       line_coord(ax, line, k, src.e0, src.e1, &a, &b, &c);
       return src.at(a, b, c, v);
@@ -196,7 +243,7 @@ __device__ __forceinline__ void pass(const BFrags<BF16, KIN, NOUT>& f, const Til
   }
 }
 
-template <int NP, int NQ, bool GEN, bool BF16>
+template <int NP, int NQ, bool GEN, int KIND>
 __global__ void __launch_bounds__(32 * kMmaWarps) mma_apply_kernel(const Tables<float, NP, NQ> tab, const MeshDev m,
                                                                    const Geom<float> geo,
                                                                    const int* __restrict__ cells, int n_vec, int n_vb,
@@ -215,10 +262,10 @@ __global__ void __launch_bounds__(32 * kMmaWarps) mma_apply_kernel(const Tables<
 
   // ---- extraction fused with the x pass of N: S0[i3][i2][q1] ----
   {
-    BFrags<BF16, NP, NQ> f;
+    BFrags<KIND, NP, NQ> f;
     load_bfrags(f, tab.N, false);
     const Tile dst{S0q.p, NQ, NP, NP};
-    constexpr int NT = BFrags<BF16, NP, NQ>::NT;
+    constexpr int NT = BFrags<KIND, NP, NQ>::NT;
     for (int line = warp; line < NP * NP; line += kMmaWarps) {
       const int i2 = line % NP, i3 = line / NP;
       const int gy = node_coord(cy, i2, P, m.Ny, m.periodic), gz = node_coord(cz, i3, P, m.Nz, m.periodic);
@@ -227,7 +274,7 @@ __global__ void __launch_bounds__(32 * kMmaWarps) mma_apply_kernel(const Tables<
       DFrag<NT> acc;
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) acc.d[nt][0] = acc.d[nt][1] = acc.d[nt][2] = acc.d[nt][3] = 0.f;
-      line_mma<BF16, NP, NQ>(f, acc, [&](int v, int k) {
+      line_mma<KIND, NP, NQ>(f, acc, [&](int v, int k) {
         const int gx = node_coord(cx, k, P, m.Nx, m.periodic);
         const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
         return (v0 + v < n_vec && !con) ? __ldg(X + (row + gx) * n_vec + v0 + v) : 0.f;
@@ -237,29 +284,29 @@ __global__ void __launch_bounds__(32 * kMmaWarps) mma_apply_kernel(const Tables<
   }
   __syncthreads();
   {  // y pass of N: S1[i3][q2][q1]
-    BFrags<BF16, NP, NQ> f;
+    BFrags<KIND, NP, NQ> f;
     load_bfrags(f, tab.N, false);
-    pass<BF16, NP, NQ, false>(f, Tile{S0q.p, NQ, NP, NP}, Tile{S1q.p, NQ, NQ, NP}, 1, NQ * NP);
+    pass<KIND, NP, NQ, false>(f, Tile{S0q.p, NQ, NP, NP}, Tile{S1q.p, NQ, NQ, NP}, 1, NQ * NP);
   }
   __syncthreads();
   {  // z pass of N: T[q3][q2][q1]
-    BFrags<BF16, NP, NQ> f;
+    BFrags<KIND, NP, NQ> f;
     load_bfrags(f, tab.N, false);
-    pass<BF16, NP, NQ, false>(f, Tile{S1q.p, NQ, NQ, NP}, ST, 2, NQ * NQ);
+    pass<KIND, NP, NQ, false>(f, Tile{S1q.p, NQ, NQ, NP}, ST, 2, NQ * NQ);
   }
   __syncthreads();
   {  // gradients along x (-> S0) and y (-> S1)
-    BFrags<BF16, NQ, NQ> f;
+    BFrags<KIND, NQ, NQ> f;
     load_bfrags(f, tab.D, false);
-    pass<BF16, NQ, NQ, false>(f, ST, S0q, 0, NQ * NQ);
-    pass<BF16, NQ, NQ, false>(f, ST, S1q, 1, NQ * NQ);
+    pass<KIND, NQ, NQ, false>(f, ST, S0q, 0, NQ * NQ);
+    pass<KIND, NQ, NQ, false>(f, ST, S1q, 1, NQ * NQ);
   }
   __syncthreads();
   {  // z-lines: gradient along z, quadrature-point operation, transposed z pass with c T as accumulator
-    BFrags<BF16, NQ, NQ> fd, fdt;
+    BFrags<KIND, NQ, NQ> fd, fdt;
     load_bfrags(fd, tab.D, false);
     load_bfrags(fdt, tab.D, true);
-    constexpr int NT = BFrags<BF16, NQ, NQ>::NT;
+    constexpr int NT = BFrags<KIND, NQ, NQ>::NT;
     float g00, g01, g02, g11, g12, g22;
     if (!GEN) {
       g00 = geo.cellG[e * 6 + 0]; g01 = geo.cellG[e * 6 + 1]; g02 = geo.cellG[e * 6 + 2];
@@ -271,7 +318,7 @@ __global__ void __launch_bounds__(32 * kMmaWarps) mma_apply_kernel(const Tables<
       DFrag<NT> t2, ct;
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) t2.d[nt][0] = t2.d[nt][1] = t2.d[nt][2] = t2.d[nt][3] = 0.f;
-      line_mma<BF16, NQ, NQ>(fd, t2, [&](int v, int k) { return ST.at(q1, q2, k, v); });
+      line_mma<KIND, NQ, NQ>(fd, t2, [&](int v, int k) { return ST.at(q1, q2, k, v); });
       // point operation on the fragment elements (each (v, q3) owned by one thread)
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt)
@@ -297,43 +344,43 @@ __global__ void __launch_bounds__(32 * kMmaWarps) mma_apply_kernel(const Tables<
       // the z-line of T is no longer needed: park h2 there, reload it as the A operand
       for_frag<NT, NQ>(t2, [&](int v, int n, float& x) { ST.at(q1, q2, n, v) = x; });
       __syncwarp();
-      line_mma<BF16, NQ, NQ>(fdt, ct, [&](int v, int k) { return ST.at(q1, q2, k, v); });
+      line_mma<KIND, NQ, NQ>(fdt, ct, [&](int v, int k) { return ST.at(q1, q2, k, v); });
       __syncwarp();
       for_frag<NT, NQ>(ct, [&](int v, int n, float& x) { ST.at(q1, q2, n, v) = x; });
     }
   }
   __syncthreads();
   {  // transposed x pass of D~, then transposed y pass, accumulated into T
-    BFrags<BF16, NQ, NQ> f;
+    BFrags<KIND, NQ, NQ> f;
     load_bfrags(f, tab.D, true);
-    pass<BF16, NQ, NQ, true>(f, S0q, ST, 0, NQ * NQ);
+    pass<KIND, NQ, NQ, true>(f, S0q, ST, 0, NQ * NQ);
     __syncthreads();
-    pass<BF16, NQ, NQ, true>(f, S1q, ST, 1, NQ * NQ);
+    pass<KIND, NQ, NQ, true>(f, S1q, ST, 1, NQ * NQ);
   }
   __syncthreads();
   {  // transposed z pass of N: S1[i3][q2][q1]
-    BFrags<BF16, NQ, NP> f;
+    BFrags<KIND, NQ, NP> f;
     load_bfrags(f, tab.N, true);
-    pass<BF16, NQ, NP, false>(f, ST, Tile{S1q.p, NQ, NQ, NP}, 2, NQ * NQ);
+    pass<KIND, NQ, NP, false>(f, ST, Tile{S1q.p, NQ, NQ, NP}, 2, NQ * NQ);
   }
   __syncthreads();
   {  // transposed y pass of N: S0[i3][i2][q1]
-    BFrags<BF16, NQ, NP> f;
+    BFrags<KIND, NQ, NP> f;
     load_bfrags(f, tab.N, true);
-    pass<BF16, NQ, NP, false>(f, Tile{S1q.p, NQ, NQ, NP}, Tile{S0q.p, NQ, NP, NP}, 1, NQ * NP);
+    pass<KIND, NQ, NP, false>(f, Tile{S1q.p, NQ, NQ, NP}, Tile{S0q.p, NQ, NP, NP}, 1, NQ * NP);
   }
   __syncthreads();
   {  // transposed x pass of N fused with assembly
-    BFrags<BF16, NQ, NP> f;
+    BFrags<KIND, NQ, NP> f;
     load_bfrags(f, tab.N, true);
     const Tile src{S0q.p, NQ, NP, NP};
-    constexpr int NT = BFrags<BF16, NQ, NP>::NT;
+    constexpr int NT = BFrags<KIND, NQ, NP>::NT;
     for (int line = warp; line < NP * NP; line += kMmaWarps) {
       const int i2 = line % NP, i3 = line / NP;
       DFrag<NT> acc;
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) acc.d[nt][0] = acc.d[nt][1] = acc.d[nt][2] = acc.d[nt][3] = 0.f;
-      line_mma<BF16, NQ, NP>(f, acc, [&](int v, int k) { return src.at(k, i2, i3, v); });
+      line_mma<KIND, NQ, NP>(f, acc, [&](int v, int k) { return src.at(k, i2, i3, v); });
       const int gy = node_coord(cy, i2, P, m.Ny, m.periodic), gz = node_coord(cz, i3, P, m.Nz, m.periodic);
       const bool con_yz = on_boundary(gy, m.Ny, m.periodic) || on_boundary(gz, m.Nz, m.periodic);
       const bool first_yz = first_along(cy, m.ny, i2, P, m.periodic, m.last_odd_y) &&
@@ -352,9 +399,9 @@ __global__ void __launch_bounds__(32 * kMmaWarps) mma_apply_kernel(const Tables<
   }
 }
 
-template <int NP, int NQ, bool GEN, bool BF16>
+template <int NP, int NQ, bool GEN, int KIND>
 cudaError_t launch_mma(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s) {
-  auto kern = mma_apply_kernel<NP, NQ, GEN, BF16>;
+  auto kern = mma_apply_kernel<NP, NQ, GEN, KIND>;
   const size_t smem = (size_t)3 * NQ * NQ * NQ * kMmaVB * sizeof(float);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
   static size_t configured = 0;

@@ -376,7 +376,7 @@ extern "C" fe_status fe_set_potential(fe_ctx* c, const double* Vq) {
 
 extern "C" fe_status fe_set_mode(fe_ctx* c, fe_mode m) {
   if (!c) return FE_EINVAL;
-  if (m != FE_FP64 && m != FE_FP32 && m != FE_TF32 && m != FE_BF16) return FE_EINVAL;
+  if (m != FE_FP64 && m != FE_FP32 && m != FE_TF32 && m != FE_BF16 && m != FE_TF32X3) return FE_EINVAL;
   c->mode = m;
   return FE_OK;
 }

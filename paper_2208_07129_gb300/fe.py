@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libfe.so")
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOTCONV, FE_EBREAKDOWN, FE_ENONFINITE, FE_ETIMEOUT, FE_EUNSUPPORTED = range(9)
 FE_BC_DIRICHLET0, FE_BC_PERIODIC = 0, 1
 FE_QUAD_GAUSS, FE_QUAD_GLL = 0, 1
-FE_FP64, FE_FP32, FE_TF32, FE_BF16 = 0, 1, 2, 3
-MODES = {"fp64": FE_FP64, "fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16}
+FE_FP64, FE_FP32, FE_TF32, FE_BF16, FE_TF32X3 = 0, 1, 2, 3, 4
+MODES = {"fp64": FE_FP64, "fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16, "tf32x3": FE_TF32X3}
 
 
 class FeError(RuntimeError):

@@ -39,7 +39,7 @@ def _problem(fe, nx=3, p=4, nq=6, n_vec=6, distorted=False, seed=0):
 
 
 @pytest.mark.parametrize("precond,inner", [("jacobi", "fp64"), ("none", "fp64"), ("jacobi", "fp32"),
-                                           ("jacobi", "tf32"), ("jacobi", "bf16")])
+                                           ("jacobi", "tf32"), ("jacobi", "bf16"), ("jacobi", "tf32x3")])
 def test_pcg_solution(fe, precond, inner):
     ctx, B, Xref = _problem(fe, distorted=(inner != "fp64"))
     try:
