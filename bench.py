@@ -221,6 +221,21 @@ def cpu_baseline(w, budget_s: float = 12.0):
     return o.result(n, o.run(n))
 
 
+def cpu_pcg_extrapolated(w, iterations: int, budget_s: float = 8.0) -> dict:
+    """The oracle's time to solution for Jacobi-PCG on `w`, extrapolated: one
+    full oracle apply (rate measured on a bounded sample of rows) times the
+    FP64 iteration count of the GPU solve.  Vector updates and reductions are
+    not counted, so the figure is a lower bound."""
+    o = OracleSample(w)
+    n = o.sized(budget_s)
+    dt = o.run(n)
+    s_apply = dt / n * w.num_dofs
+    return {"kind": "oracle", "cores": o.orc.num_threads(), "extrapolated": True,
+            "seconds_per_apply": s_apply, "iterations": iterations, "seconds_extrapolated": s_apply * iterations,
+            "sample": f"{n} of {w.num_dofs} rows of A X with {w.n_vec} columns ({dt:.1f} s), scaled to all rows; "
+                      f"vector updates not counted"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle on the host cores (rank 0 only); each
     step is a bounded sample of rows of the 32^3 workload."""
@@ -274,7 +289,7 @@ def time_mode(fe, torch, ctx, w, mode, steps, warmup, world):
     return ms, per, X, Y
 
 
-def solve_bench(fe, torch, sub_cols: int = 16):
+def solve_bench(fe, torch, sub_cols: int = 16, cpu: bool = True):
     """Time to relative residual 1e-8 (FP64 operator as judge) for the block
     PCG solve of the 24^3, p=6, 128-column problem: mixed precision (FP32 inner
     PCG with Jacobi, FP64 refinement) run to the end, and FP64 Jacobi-PCG
@@ -306,6 +321,8 @@ def solve_bench(fe, torch, sub_cols: int = 16):
                               "seconds_extrapolated": rs["iterations"] * t_it + (t[2] - 2 * t_it),
                               "extrapolated": True}
         out["speedup_mixed_vs_fp64"] = out["fp64_jacobi"]["seconds_extrapolated"] / r["seconds"]
+        if cpu:
+            out["cpu_oracle_fp64_jacobi"] = cpu_pcg_extrapolated(w, rs["iterations"])
         # learned cell-patch preconditioner: trained on this operator's own Jacobi-PCG
         # trajectories (8 random right-hand sides, snapshots every 32 iterations,
         # energy-norm objective, checkpoint picked on 4 held-out right-hand sides),
@@ -588,7 +605,7 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and not args.no_solve:
-        out["pcg"] = solve_bench(fe, torch)
+        out["pcg"] = solve_bench(fe, torch, cpu=not args.no_cpu)
     if rank == 0 and not args.no_batch:
         out["batch"] = batch_bench(fe, torch)
     if rank == 0 and not args.no_distorted:
