@@ -56,13 +56,34 @@ __device__ __forceinline__ bool on_boundary(int g, int N, int periodic) {
   return !periodic && (g == 0 || g == N - 1);
 }
 
+// Scatter of the scaled product for one node: the first writer of the node
+// (colour order) stores a M^-1/2 (cell sum) + b X + c Y_old (0 on constrained
+// rows), later writers add their a M^-1/2 (cell sum).  b X and c Y are only
+// read when the coefficient is nonzero, so Y may start uninitialised when c = 0.
+template <typename T>
+__device__ __forceinline__ void scaled_store(T* dst, const T* x, T val, bool first, bool con, const Scale<T>& sc) {
+  if (first) {
+    if (con) {
+      *dst = T(0);
+    } else {
+      if (sc.b != T(0)) val += sc.b * __ldg(x);
+      if (sc.c != T(0)) val += sc.c * *dst;
+      *dst = val;
+    }
+  } else if (!con) {
+    *dst += val;
+  }
+}
+
 // The work of one CTA: cell e, vector block vb of B vectors; thread (v, ty) of
 // a B x nty thread block; smem holds 3 n_q^3 x B values.  Shared by the
-// per-colour launches below and by the persistent batch kernel.
-template <typename T, int NP, int NQ, bool GEN>
+// per-colour launches below and by the persistent batch kernel.  With SC the
+// gather scales X by M^-1/2 and the scatter writes the scaled product
+// a M^-1/2 (.) + b X + c Y (see Scale).
+template <typename T, int NP, int NQ, bool GEN, bool SC = false>
 __device__ __forceinline__ void cell_body(const Tables<T, NP, NQ>& tab, const MeshDev& m, const Geom<T>& geo, int e,
                                           int vb, int B, int v, int ty, int nty, int n_vec, const T* __restrict__ X,
-                                          T* __restrict__ Y, T* smem) {
+                                          T* __restrict__ Y, T* smem, const Scale<T>& sc = Scale<T>{}) {
   constexpr int P = NP - 1;
   constexpr int NQ3 = NQ * NQ * NQ;
   T* ST = smem;
@@ -84,6 +105,7 @@ __device__ __forceinline__ void cell_body(const Tables<T, NP, NQ>& tab, const Me
       const int gx = node_coord(cx, i1, P, m.Nx, m.periodic);
       const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
       u[i1] = (active && !con) ? __ldg(X + (row + gx) * n_vec + vg) : T(0);
+      if constexpr (SC) u[i1] *= __ldg(sc.msq + row + gx);
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -264,8 +286,12 @@ __device__ __forceinline__ void cell_body(const Tables<T, NP, NQ>& tab, const Me
       const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
       const bool first = first_yz && first_along(cx, m.nx, i, P, m.periodic, m.last_odd_x);
       T* dst = Y + (row + gx) * n_vec + vg;
-      if (first) *dst = con ? T(0) : s;
-      else if (!con) *dst += s;
+      if constexpr (SC) {
+        scaled_store(dst, X + (row + gx) * n_vec + vg, sc.a * __ldg(sc.msq + row + gx) * s, first, con, sc);
+      } else {
+        if (first) *dst = con ? T(0) : s;
+        else if (!con) *dst += s;
+      }
     }
   }
 }
@@ -278,6 +304,17 @@ __global__ void __launch_bounds__(256) cell_apply_kernel(const Tables<T, NP, NQ>
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cell_body<T, NP, NQ, GEN>(tab, m, geo, cells[blockIdx.x / n_vb], blockIdx.x % n_vb, blockDim.x, threadIdx.x,
                             threadIdx.y, blockDim.y, n_vec, X, Y, reinterpret_cast<T*>(smem_raw));
+}
+
+// The scaled product of the Chebyshev filter, Y = a M^-1/2 A M^-1/2 X + b X + c Y.
+template <typename T, int NP, int NQ, bool GEN>
+__global__ void __launch_bounds__(256) cell_apply_scaled_kernel(const Tables<T, NP, NQ> tab, const MeshDev m,
+                                                                const Geom<T> geo, const int* __restrict__ cells,
+                                                                int n_vec, int n_vb, const T* __restrict__ X,
+                                                                T* __restrict__ Y, const Scale<T> sc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cell_body<T, NP, NQ, GEN, true>(tab, m, geo, cells[blockIdx.x / n_vb], blockIdx.x % n_vb, blockDim.x, threadIdx.x,
+                                  threadIdx.y, blockDim.y, n_vec, X, Y, reinterpret_cast<T*>(smem_raw), sc);
 }
 
 // diag(A): one thread per (cell, local node), sum over the quadrature points of

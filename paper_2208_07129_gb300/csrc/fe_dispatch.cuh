@@ -40,9 +40,12 @@ inline int pick_vb(int want, int n_vec) {
   return vb;
 }
 
-template <typename T, int NP, int NQ, bool GEN>
-cudaError_t launch_apply(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaStream_t s, int want_vb, int want_lines) {
-  auto kern = cell_apply_kernel<T, NP, NQ, GEN>;
+template <typename T, int NP, int NQ, bool GEN, bool SC = false>
+cudaError_t launch_apply(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaStream_t s, int want_vb, int want_lines,
+                         const Scale<T>& sc = Scale<T>{}) {
+  const void* kern;
+  if constexpr (SC) kern = reinterpret_cast<const void*>(cell_apply_scaled_kernel<T, NP, NQ, GEN>);
+  else kern = reinterpret_cast<const void*>(cell_apply_kernel<T, NP, NQ, GEN>);
   const int vb = pick_vb<T, NQ>(want_vb, n_vec);
   int nty = want_lines;
   if (vb * nty > 256) nty = 256 / vb;
@@ -62,8 +65,12 @@ cudaError_t launch_apply(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaStrea
     if (n == 0) continue;
     const long long blocks = (long long)n * n_vb;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)blocks, dim3(vb, nty), smem, s>>>(tab, c->mdev, geo, c->d_cells + c->colors.offset[k], n_vec,
-                                                       n_vb, X, Y);
+    if constexpr (SC)
+      cell_apply_scaled_kernel<T, NP, NQ, GEN><<<(unsigned)blocks, dim3(vb, nty), smem, s>>>(
+          tab, c->mdev, geo, c->d_cells + c->colors.offset[k], n_vec, n_vb, X, Y, sc);
+    else
+      cell_apply_kernel<T, NP, NQ, GEN><<<(unsigned)blocks, dim3(vb, nty), smem, s>>>(
+          tab, c->mdev, geo, c->d_cells + c->colors.offset[k], n_vec, n_vb, X, Y);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -59,12 +59,13 @@ __device__ __forceinline__ void eo_apply(const EOTab<T, NO, NI>& t, const T* in,
   }
 }
 
-// Same as cell_body (identical data flow, tiles and assembly), with every 1D
-// contraction in even-odd form.
-template <typename T, int NP, int NQ, bool GEN>
+// Same as cell_body (identical data flow, tiles and assembly, the same SC
+// epilogue), with every 1D contraction in even-odd form.
+template <typename T, int NP, int NQ, bool GEN, bool SC = false>
 __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, const MeshDev& m, const Geom<T>& geo,
                                              int e, int vb, int B, int v, int ty, int nty, int n_vec,
-                                             const T* __restrict__ X, T* __restrict__ Y, T* smem) {
+                                             const T* __restrict__ X, T* __restrict__ Y, T* smem,
+                                             const Scale<T>& sc = Scale<T>{}) {
   constexpr int P = NP - 1;
   constexpr int NQ3 = NQ * NQ * NQ;
   T* ST = smem;
@@ -86,6 +87,7 @@ __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, con
       const int gx = node_coord(cx, i1, P, m.Nx, m.periodic);
       const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
       u[i1] = (active && !con) ? __ldg(X + (row + gx) * n_vec + vg) : T(0);
+      if constexpr (SC) u[i1] *= __ldg(sc.msq + row + gx);
     }
     eo_apply<T, NQ, NP, 1>(tab.N, u, a);
 #pragma unroll
@@ -221,8 +223,12 @@ __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, con
       const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
       const bool first = first_yz && first_along(cx, m.nx, i, P, m.periodic, m.last_odd_x);
       T* dst = Y + (row + gx) * n_vec + vg;
-      if (first) *dst = con ? T(0) : o[i];
-      else if (!con) *dst += o[i];
+      if constexpr (SC) {
+        scaled_store(dst, X + (row + gx) * n_vec + vg, sc.a * __ldg(sc.msq + row + gx) * o[i], first, con, sc);
+      } else {
+        if (first) *dst = con ? T(0) : o[i];
+        else if (!con) *dst += o[i];
+      }
     }
   }
 }
@@ -235,6 +241,18 @@ __global__ void __launch_bounds__(256) cell_apply_eo_kernel(const EOTables<T, NP
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cell_body_eo<T, NP, NQ, GEN>(tab, m, geo, cells[blockIdx.x / n_vb], blockIdx.x % n_vb, blockDim.x, threadIdx.x,
                                threadIdx.y, blockDim.y, n_vec, X, Y, reinterpret_cast<T*>(smem_raw));
+}
+
+// The scaled product of the Chebyshev filter with even-odd contractions.
+template <typename T, int NP, int NQ, bool GEN>
+__global__ void __launch_bounds__(256) cell_apply_eo_scaled_kernel(const EOTables<T, NP, NQ> tab, const MeshDev m,
+                                                                   const Geom<T> geo, const int* __restrict__ cells,
+                                                                   int n_vec, int n_vb, const T* __restrict__ X,
+                                                                   T* __restrict__ Y, const Scale<T> sc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cell_body_eo<T, NP, NQ, GEN, true>(tab, m, geo, cells[blockIdx.x / n_vb], blockIdx.x % n_vb, blockDim.x,
+                                     threadIdx.x, threadIdx.y, blockDim.y, n_vec, X, Y,
+                                     reinterpret_cast<T*>(smem_raw), sc);
 }
 
 // Host: even-odd tables of an NO x NI row-major matrix M with symmetry S.
@@ -265,10 +283,12 @@ EOTables<T, NP, NQ> make_eotables(const fe_ctx* c) {
   return t;
 }
 
-template <typename T, int NP, int NQ, bool GEN>
+template <typename T, int NP, int NQ, bool GEN, bool SC = false>
 cudaError_t launch_apply_eo(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaStream_t s, int want_vb,
-                            int want_lines) {
-  auto kern = cell_apply_eo_kernel<T, NP, NQ, GEN>;
+                            int want_lines, const Scale<T>& sc = Scale<T>{}) {
+  const void* kern;
+  if constexpr (SC) kern = reinterpret_cast<const void*>(cell_apply_eo_scaled_kernel<T, NP, NQ, GEN>);
+  else kern = reinterpret_cast<const void*>(cell_apply_eo_kernel<T, NP, NQ, GEN>);
   const int vb = pick_vb<T, NQ>(want_vb, n_vec);
   int nty = want_lines;
   if (vb * nty > 256) nty = 256 / vb;
@@ -288,8 +308,12 @@ cudaError_t launch_apply_eo(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaSt
     if (n == 0) continue;
     const long long blocks = (long long)n * n_vb;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)blocks, dim3(vb, nty), smem, s>>>(tab, c->mdev, geo, c->d_cells + c->colors.offset[k], n_vec,
-                                                       n_vb, X, Y);
+    if constexpr (SC)
+      cell_apply_eo_scaled_kernel<T, NP, NQ, GEN><<<(unsigned)blocks, dim3(vb, nty), smem, s>>>(
+          tab, c->mdev, geo, c->d_cells + c->colors.offset[k], n_vec, n_vb, X, Y, sc);
+    else
+      cell_apply_eo_kernel<T, NP, NQ, GEN><<<(unsigned)blocks, dim3(vb, nty), smem, s>>>(
+          tab, c->mdev, geo, c->d_cells + c->colors.offset[k], n_vec, n_vb, X, Y);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

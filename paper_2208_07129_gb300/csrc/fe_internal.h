@@ -44,6 +44,15 @@ struct Geom {
   const T* ptC;
 };
 
+// Epilogue of the scaled product of the Chebyshev filter,
+//   Y = a M^-1/2 A M^-1/2 X + b X + c Y   (msq = M^-1/2, one value per DoF),
+// fused into the gather (X M^-1/2) and the first-writer scatter.
+template <typename T>
+struct Scale {
+  const T* msq;
+  T a, b, c;
+};
+
 struct ColorSet {
   int n_colors;
   std::vector<int> offset;  // n_colors + 1
@@ -87,7 +96,7 @@ struct fe_ctx {
   size_t n_dofs, n_cells;
   fe::MeshDev mdev;
   // host FP64 data
-  std::vector<double> gll, qx, qw, N1, D1;   // N1[q*np+i], D1[q*nq+k] (unfolded)
+  std::vector<double> gll, wgll, qx, qw, N1, D1;   // N1[q*np+i], D1[q*nq+k] (unfolded)
   std::vector<double> Nf, Df;                // folded
   std::vector<double> vertices;              // copy of the vertex array (general)
   double box_lo[3] = {0, 0, 0}, box_h[3] = {1, 1, 1};  // uniform box: corner and cell size
@@ -111,6 +120,13 @@ struct fe_ctx {
   fe_mode inner_mode = FE_FP32;   // arithmetic of the inner solve (refinement)
   fe::SolveWs ws;
   fe::LearnedPrecond* learned = nullptr;
+  // eigenvalue layer: GLL diagonal mass (host), M^-1/2 on the device, and the
+  // dense linear-algebra handles of the subspace iteration (created on first use)
+  std::vector<double> mass;
+  double* d_msq64 = nullptr;
+  float* d_msq32 = nullptr;
+  void* blas = nullptr;
+  void* solver = nullptr;
   // launch shape per mode (vectors per CTA, lines per CTA)
   int vb64 = 8, nty64 = 16, vb32 = 8, nty32 = 32;
   int fp32_variant = 0;   // 0 / 1: line kernel, 2: register-plane kernel
@@ -123,6 +139,13 @@ cudaError_t apply_cc_f64(const fe_ctx* c, const double* X, double* Y, int n_vec,
 cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);
 cudaError_t diagonal_f64(const fe_ctx* c, double* diag, cudaStream_t s);
 cudaError_t apply_mma_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s, fe_mode mode);
+cudaError_t apply_scaled_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, const Scale<double>& sc,
+                             cudaStream_t s);
+cudaError_t apply_scaled_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, const Scale<float>& sc,
+                             cudaStream_t s);
+// GLL diagonal mass of Sec. 4.3 into c->mass (host, FP64; constrained rows 1).
+void build_gll_mass(fe_ctx* c);
+void free_eig(fe_ctx* c);
 // Solver workspace and the learned preconditioner (fe_solve.cu / fe_learn.cu).
 cudaError_t solver_workspace(fe_ctx* c, int nv);
 void free_solver_workspace(fe_ctx* c);

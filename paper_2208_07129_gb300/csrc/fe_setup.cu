@@ -172,6 +172,49 @@ cudaError_t upload_point_coeff(fe_ctx* c, const std::vector<double>& ptC) {
   return e;
 }
 
+// Diagonal mass by the (p+1)-point GLL rule on the element nodes (Sec. 4.3):
+// node (i1, i2, i3) of cell e contributes w_i1 w_i2 w_i3 det J_e(node).
+void build_gll_mass(fe_ctx* c) {
+  if (!c->mass.empty()) return;
+  const int P = c->p, np = c->np;
+  const int Nx = c->mdev.Nx, Ny = c->mdev.Ny, Nz = c->mdev.Nz;
+  fe_mesh_desc md{};
+  c->mass.assign(c->n_dofs, 0.0);
+  for (int cz = 0; cz < c->nz; ++cz)
+    for (int cy = 0; cy < c->ny; ++cy)
+      for (int cx = 0; cx < c->nx; ++cx) {
+        double X[8][3];
+        for (int k = 0; k < 8; ++k) {
+          if (c->general) {
+            corner(c, cx, cy, cz, k, &md, X[k]);
+          } else {
+            const int idx[3] = {cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1)};
+            for (int d = 0; d < 3; ++d) X[k][d] = c->box_lo[d] + c->box_h[d] * idx[d];
+          }
+        }
+        for (int i3 = 0; i3 < np; ++i3)
+          for (int i2 = 0; i2 < np; ++i2)
+            for (int i1 = 0; i1 < np; ++i1) {
+              const double xi[3] = {c->gll[i1], c->gll[i2], c->gll[i3]};
+              double x[3], J[3][3];
+              trilinear_map(X, xi, x, J);
+              const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                 J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+              int g[3] = {cx * P + i1, cy * P + i2, cz * P + i3};
+              if (c->periodic) { g[0] %= Nx; g[1] %= Ny; g[2] %= Nz; }
+              c->mass[g[0] + (size_t)Nx * (g[1] + (size_t)Ny * g[2])] +=
+                  c->wgll[i1] * c->wgll[i2] * c->wgll[i3] * det;
+            }
+      }
+  if (!c->periodic)
+    for (int gz = 0; gz < Nz; ++gz)
+      for (int gy = 0; gy < Ny; ++gy)
+        for (int gx = 0; gx < Nx; ++gx)
+          if (gx == 0 || gy == 0 || gz == 0 || gx == Nx - 1 || gy == Ny - 1 || gz == Nz - 1)
+            c->mass[gx + (size_t)Nx * (gy + (size_t)Ny * gz)] = 1.0;
+}
+
 }  // namespace fe
 
 using namespace fe;
@@ -220,9 +263,8 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
   }
 
   // ---- 1D tables ----
-  c->gll.resize(np); c->qx.resize(nq); c->qw.resize(nq);
-  std::vector<double> wgll(np);
-  gll_rule(np, c->gll.data(), wgll.data());
+  c->gll.resize(np); c->wgll.resize(np); c->qx.resize(nq); c->qw.resize(nq);
+  gll_rule(np, c->gll.data(), c->wgll.data());
   if (quad->kind == FE_QUAD_GAUSS) gauss_rule(nq, c->qx.data(), c->qw.data());
   else gll_rule(nq, c->qx.data(), c->qw.data());
   c->N1.resize(nq * np); c->D1.resize(nq * nq); c->Nf.resize(nq * np); c->Df.resize(nq * nq);
@@ -323,6 +365,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
     if (ev) cudaEventDestroy(ev);
   free_solver_workspace(c);
   free_learned(c);
+  free_eig(c);
   delete c;
 }
 

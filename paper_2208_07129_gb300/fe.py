@@ -71,6 +71,20 @@ class fe_batch_info(ctypes.Structure):
                 ("device_status", ctypes.c_int)]
 
 
+class fe_chfsi_desc(ctypes.Structure):
+    _fields_ = [("n_wanted", ctypes.c_int), ("degree", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("lanczos_steps", ctypes.c_int), ("filter_mode", ctypes.c_int),
+                ("fp32_switch", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
+class fe_chfsi_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("filter_applies", ctypes.c_int), ("fp32_passes", ctypes.c_int),
+                ("converged", ctypes.c_int), ("max_residual", ctypes.c_double), ("lambda_min", ctypes.c_double),
+                ("lambda_u", ctypes.c_double), ("lambda_max", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("seconds_filter", ctypes.c_double), ("seconds_orth", ctypes.c_double),
+                ("seconds_rr", ctypes.c_double)]
+
+
 class fe_quad_desc(ctypes.Structure):
     _fields_ = [("n_q", ctypes.c_int), ("kind", ctypes.c_int)]
 
@@ -123,6 +137,13 @@ def lib() -> ctypes.CDLL:
         "fe_precond_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
         "fe_precond_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
         "fe_mlp_gradients": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
+        "fe_mass_gll": (ctypes.c_int, [_VP, _DP]),
+        "fe_apply_scaled": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, _VP]),
+        "fe_chebyshev_filter": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, _VP]),
+        "fe_chfsi": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(fe_chfsi_desc), _DP, _DP,
+                                    ctypes.POINTER(fe_chfsi_info), _VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -388,6 +409,57 @@ def fe_batch_stats(batch: int, n: int) -> dict:
 
 def fe_batch_destroy(batch: int) -> None:
     lib().fe_batch_destroy(batch)
+
+
+def fe_mass_gll(ctx: int) -> np.ndarray:
+    """Diagonal of the GLL-integrated overlap matrix (host FP64; constrained rows 1)."""
+    m = np.zeros(fe_num_dofs(ctx))
+    _check(lib().fe_mass_gll(ctx, m.ctypes.data_as(_DP)), "fe_mass_gll")
+    return m
+
+
+def fe_apply_scaled(ctx: int, X, Y, a: float, b: float = 0.0, c: float = 0.0, stream=None) -> None:
+    """Y = a M^-1/2 A M^-1/2 X + b X + c Y on the device (mode FP64 or FP32)."""
+    _check_block(ctx, X, "X")
+    _check_block(ctx, Y, "Y")
+    if X.shape != Y.shape:
+        raise ValueError("X and Y must have the same shape")
+    _check(lib().fe_apply_scaled(ctx, X.data_ptr(), Y.data_ptr(), X.shape[1], float(a), float(b), float(c),
+                                 _stream_ptr(stream)), "fe_apply_scaled")
+
+
+def fe_chebyshev_filter(ctx: int, X, Y, degree: int, lambda_min: float, lambda_u: float, lambda_max: float,
+                        stream=None) -> None:
+    """X <- p_m(M^-1/2 A M^-1/2) X (Algorithm 6's filter); Y is scratch."""
+    _check_block(ctx, X, "X")
+    _check_block(ctx, Y, "Y")
+    if X.shape != Y.shape:
+        raise ValueError("X and Y must have the same shape")
+    _check(lib().fe_chebyshev_filter(ctx, X.data_ptr(), Y.data_ptr(), X.shape[1], degree, lambda_min, lambda_u,
+                                     lambda_max, _stream_ptr(stream)), "fe_chebyshev_filter")
+
+
+def fe_chfsi(ctx: int, U, n_wanted: int, degree: int, tol: float, max_iter: int = 50, lanczos_steps: int = 20,
+             filter_mode="fp64", fp32_switch: float = 0.0, seed: int = 1, stream=None) -> dict:
+    """Chebyshev-filtered subspace iteration (Algorithm 6) on U (CUDA float64,
+    (num_dofs, k)); returns the Ritz values, residuals and the run info.
+    Raises unless the status is FE_OK or FE_ENOTCONV (reported)."""
+    import torch
+    if not U.is_cuda or U.dtype != torch.float64 or not U.is_contiguous() or U.dim() != 2 \
+            or U.shape[0] != fe_num_dofs(ctx):
+        raise ValueError("U: need a contiguous CUDA float64 tensor of shape (num_dofs, k)")
+    k = U.shape[1]
+    d = fe_chfsi_desc(n_wanted, degree, tol, max_iter, lanczos_steps, MODES[filter_mode], fp32_switch, seed)
+    info = fe_chfsi_info()
+    lam = np.zeros(k)
+    res = np.zeros(k)
+    st = lib().fe_chfsi(ctx, U.data_ptr(), k, ctypes.byref(d), lam.ctypes.data_as(_DP), res.ctypes.data_as(_DP),
+                        ctypes.byref(info), _stream_ptr(stream))
+    if st not in (FE_OK, FE_ENOTCONV):
+        raise FeError(st, "fe_chfsi")
+    out = {f: getattr(info, f) for f, _ in fe_chfsi_info._fields_}
+    out.update(status=st, eigenvalues=lam, residuals=res)
+    return out
 
 
 def fe_last_device_status(ctx: int) -> int:

@@ -68,3 +68,13 @@ def test_null_arguments(libfe):
     assert libfe.fe_setup(None, 2, None, 0.5, None) == 1
     assert libfe.fe_num_dofs(None) == 0
     libfe.fe_destroy(None)
+
+
+def test_eig_layer_null_arguments(libfe):
+    from paper_2208_07129_gb300 import fe
+    fe.lib()   # argument types
+    L = fe.lib()
+    assert L.fe_mass_gll(None, None) == fe.FE_EINVAL
+    assert L.fe_apply_scaled(None, None, None, 1, 1.0, 0.0, 0.0, None) == fe.FE_EINVAL
+    assert L.fe_chebyshev_filter(None, None, None, 1, 4, 0.0, 1.0, 2.0, None) == fe.FE_EINVAL
+    assert L.fe_chfsi(None, None, 4, None, None, None, None, None) == fe.FE_EINVAL
