@@ -121,15 +121,16 @@ __global__ void convert_kernel(const A* __restrict__ x, B* __restrict__ y, size_
 // Column residuals ||W_j - lambda_j U_j||_2: per-block partial sums of
 // squares over a slice of rows, then a fixed-order sum (deterministic).
 constexpr int kResRows = 128;
-__global__ void residual_partial_kernel(const double* __restrict__ U, const double* __restrict__ W,
-                                        const double* __restrict__ lam, size_t n, int k, double* __restrict__ part) {
+template <typename T>
+__global__ void residual_partial_kernel(const T* __restrict__ U, const T* __restrict__ W, const T* __restrict__ lam,
+                                        size_t n, int k, double* __restrict__ part) {
   __shared__ double red[8][33];
   const int col = blockIdx.x * 32 + threadIdx.x;
   double acc = 0.0;
   if (col < k) {
-    const double l = lam[col];
+    const T l = lam[col];
     for (size_t r = blockIdx.y * 8 + threadIdx.y; r < n; r += (size_t)gridDim.y * 8) {
-      const double d = W[r * k + col] - l * U[r * k + col];
+      const double d = (double)(W[r * k + col] - l * U[r * k + col]);
       acc += d * d;
     }
   }
@@ -150,10 +151,73 @@ __global__ void residual_final_kernel(const double* __restrict__ part, int k, in
   res[col] = std::sqrt(s);
 }
 
-__global__ void add_diagonal_kernel(double* __restrict__ S, int k, double shift) {
+template <typename T>
+__global__ void add_diagonal_kernel(T* __restrict__ S, int k, T shift) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < k) S[(size_t)i * k + i] += shift;
 }
+
+// The dense kernels in either precision (cuBLAS / cuSOLVER, column-major).
+template <typename T>
+struct Dense;
+template <>
+struct Dense<double> {
+  static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+                             const double* A, int lda, const double* B, int ldb, double* C, int ldc) {
+    const double one = 1.0, zero = 0.0;
+    return cublasDgemm(h, ta, tb, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc);
+  }
+  static cublasStatus_t trsm_lt(cublasHandle_t h, int m, int n, const double* R, double* B) {
+    const double one = 1.0;
+    return cublasDtrsm(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, m, n, &one,
+                       R, m, B, m);
+  }
+  static cublasStatus_t asum(cublasHandle_t h, int n, const double* x, int inc, double* r) {
+    return cublasDasum(h, n, x, inc, r);
+  }
+  static cusolverStatus_t potrf_buf(cusolverDnHandle_t h, int k, double* S, int* lw) {
+    return cusolverDnDpotrf_bufferSize(h, CUBLAS_FILL_MODE_UPPER, k, S, k, lw);
+  }
+  static cusolverStatus_t potrf(cusolverDnHandle_t h, int k, double* S, double* w, int lw, int* info) {
+    return cusolverDnDpotrf(h, CUBLAS_FILL_MODE_UPPER, k, S, k, w, lw, info);
+  }
+  static cusolverStatus_t syevd_buf(cusolverDnHandle_t h, int k, double* S, double* lam, int* lw) {
+    return cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, S, k, lam, lw);
+  }
+  static cusolverStatus_t syevd(cusolverDnHandle_t h, int k, double* S, double* lam, double* w, int lw, int* info) {
+    return cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, S, k, lam, w, lw, info);
+  }
+  static constexpr double shift = 1e-13;   // relative diagonal shift of the fallback Cholesky QR
+};
+template <>
+struct Dense<float> {
+  static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+                             const float* A, int lda, const float* B, int ldb, float* C, int ldc) {
+    const float one = 1.f, zero = 0.f;
+    return cublasSgemm(h, ta, tb, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc);
+  }
+  static cublasStatus_t trsm_lt(cublasHandle_t h, int m, int n, const float* R, float* B) {
+    const float one = 1.f;
+    return cublasStrsm(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, m, n, &one,
+                       R, m, B, m);
+  }
+  static cublasStatus_t asum(cublasHandle_t h, int n, const float* x, int inc, float* r) {
+    return cublasSasum(h, n, x, inc, r);
+  }
+  static cusolverStatus_t potrf_buf(cusolverDnHandle_t h, int k, float* S, int* lw) {
+    return cusolverDnSpotrf_bufferSize(h, CUBLAS_FILL_MODE_UPPER, k, S, k, lw);
+  }
+  static cusolverStatus_t potrf(cusolverDnHandle_t h, int k, float* S, float* w, int lw, int* info) {
+    return cusolverDnSpotrf(h, CUBLAS_FILL_MODE_UPPER, k, S, k, w, lw, info);
+  }
+  static cusolverStatus_t syevd_buf(cusolverDnHandle_t h, int k, float* S, float* lam, int* lw) {
+    return cusolverDnSsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, S, k, lam, lw);
+  }
+  static cusolverStatus_t syevd(cusolverDnHandle_t h, int k, float* S, float* lam, float* w, int lw, int* info) {
+    return cusolverDnSsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, S, k, lam, w, lw, info);
+  }
+  static constexpr float shift = 1e-5f;
+};
 
 cudaError_t handles(fe_ctx* c, cudaStream_t s, cublasHandle_t* hb, cusolverDnHandle_t* hs) {
   if (!c->blas) {
@@ -209,6 +273,9 @@ void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b
   *mx = bisect(n - 1);
 }
 
+// One precision's share of the subspace iteration: the current block U, the
+// work blocks W and T (n x k each), and the k x k dense state.
+template <typename T>
 struct Chfsi {
   fe_ctx* c;
   cudaStream_t s;
@@ -216,30 +283,41 @@ struct Chfsi {
   cusolverDnHandle_t hs;
   size_t n;
   int k;
-  double *W = nullptr, *T = nullptr, *S = nullptr, *lam = nullptr, *res = nullptr, *part = nullptr, *work = nullptr;
+  T *U = nullptr, *W = nullptr, *Tb = nullptr, *S = nullptr, *lam = nullptr, *work = nullptr;
+  double *res = nullptr, *part = nullptr;
   int* info = nullptr;
   int lwork = 0;
+  bool owns_u = false;
 
-  cudaError_t alloc() {
-    const size_t blk = n * (size_t)k * sizeof(double);
-    cudaError_t e = cudaMalloc(&W, blk);
-    if (e == cudaSuccess) e = cudaMalloc(&T, blk);
-    if (e == cudaSuccess) e = cudaMalloc(&S, (size_t)k * k * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&lam, k * sizeof(double));
+  // U: the caller's block (FP64) or nullptr to allocate one (FP32).
+  cudaError_t alloc(T* user) {
+    const size_t blk = n * (size_t)k * sizeof(T);
+    cudaError_t e = cudaSuccess;
+    if (user) U = user;
+    else { e = cudaMalloc(&U, blk); owns_u = true; }
+    if (e == cudaSuccess) e = cudaMalloc(&W, blk);
+    if (e == cudaSuccess) e = cudaMalloc(&Tb, blk);
+    if (e == cudaSuccess) e = cudaMalloc(&S, (size_t)k * k * sizeof(T));
+    if (e == cudaSuccess) e = cudaMalloc(&lam, k * sizeof(T));
     if (e == cudaSuccess) e = cudaMalloc(&res, k * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)kResRows * k * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&info, sizeof(int));
     if (e != cudaSuccess) return e;
     int l1 = 0, l2 = 0;
-    if (cusolverDnDpotrf_bufferSize(hs, CUBLAS_FILL_MODE_UPPER, k, S, k, &l1) != CUSOLVER_STATUS_SUCCESS ||
-        cusolverDnDsyevd_bufferSize(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, S, k, lam, &l2) !=
-            CUSOLVER_STATUS_SUCCESS)
+    if (Dense<T>::potrf_buf(hs, k, S, &l1) != CUSOLVER_STATUS_SUCCESS ||
+        Dense<T>::syevd_buf(hs, k, S, lam, &l2) != CUSOLVER_STATUS_SUCCESS)
       return cudaErrorUnknown;
     lwork = std::max(l1, l2);
-    return cudaMalloc(&work, std::max(1, lwork) * sizeof(double));
+    return cudaMalloc(&work, std::max(1, lwork) * sizeof(T));
   }
-  void release() {
-    for (double* p : {W, T, S, lam, res, part, work}) cudaFree(p);
+  // Frees the work blocks; the caller's block (wherever it sits among U, W
+  // and Tb after the pointer swaps) is left alone.
+  void release(const T* user) {
+    for (T* p : {U, W, Tb})
+      if (p != user) cudaFree(p);
+    for (T* p : {S, lam, work}) cudaFree(p);
+    cudaFree(res);
+    cudaFree(part);
     cudaFree(info);
   }
   int read_info() {
@@ -248,113 +326,131 @@ struct Chfsi {
     if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
     return h;
   }
+  fe_status gram(const T* A, const T* B) {   // S = A^T B
+    return Dense<T>::gemm(hb, CUBLAS_OP_N, CUBLAS_OP_T, k, k, (int)n, A, k, B, k, S, k) == CUBLAS_STATUS_SUCCESS
+               ? FE_OK : FE_ECUDA;
+  }
 
-  // Cholesky QR of U in place (U <- U R^-1 with U^T U = R^T R), twice; a
-  // Gram matrix that is not numerically positive definite gets a diagonal
-  // shift of 1e-13 trace(S) and a third pass.
-  fe_status cholqr(double* U) {
-    const double one = 1.0, zero = 0.0;
+  // Cholesky QR of U in place (U <- U R^-1 with U^T U = R^T R), twice; a Gram
+  // matrix that is not numerically positive definite gets a relative
+  // diagonal shift (Dense<T>::shift x trace) and a third pass.
+  fe_status cholqr() {
     int passes = 2;
     for (int pass = 0; pass < passes; ++pass) {
-      if (cublasDsyrk(hb, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, k, (int)n, &one, U, k, &zero, S, k) !=
-          CUBLAS_STATUS_SUCCESS)
-        return FE_ECUDA;
-      if (cusolverDnDpotrf(hs, CUBLAS_FILL_MODE_UPPER, k, S, k, work, lwork, info) != CUSOLVER_STATUS_SUCCESS)
-        return FE_ECUDA;
-      int st = read_info();
-      if (st < 0) return FE_ECUDA;
-      if (st > 0) {
-        if (cublasDsyrk(hb, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, k, (int)n, &one, U, k, &zero, S, k) !=
-            CUBLAS_STATUS_SUCCESS)
-          return FE_ECUDA;
-        double tr = 0.0;
-        if (cublasDasum(hb, k, S, k + 1, &tr) != CUBLAS_STATUS_SUCCESS) return FE_ECUDA;
-        if (!(tr > 0.0) || !std::isfinite(tr)) return FE_ENONFINITE;
-        add_diagonal_kernel<<<(k + 255) / 256, 256, 0, s>>>(S, k, 1e-13 * tr);
-        if (cusolverDnDpotrf(hs, CUBLAS_FILL_MODE_UPPER, k, S, k, work, lwork, info) != CUSOLVER_STATUS_SUCCESS)
-          return FE_ECUDA;
-        st = read_info();
-        if (st != 0) return FE_EBREAKDOWN;
-        passes = std::min(3, pass + 3);
+      fe_status st = gram(U, U);
+      if (st != FE_OK) return st;
+      if (Dense<T>::potrf(hs, k, S, work, lwork, info) != CUSOLVER_STATUS_SUCCESS) return FE_ECUDA;
+      int inf = read_info();
+      if (inf < 0) return FE_ECUDA;
+      if (inf > 0) {
+        if ((st = gram(U, U)) != FE_OK) return st;
+        T tr = 0;
+        if (Dense<T>::asum(hb, k, S, k + 1, &tr) != CUBLAS_STATUS_SUCCESS) return FE_ECUDA;
+        if (!(tr > 0) || !std::isfinite((double)tr)) return FE_ENONFINITE;
+        add_diagonal_kernel<T><<<(k + 255) / 256, 256, 0, s>>>(S, k, Dense<T>::shift * tr);
+        if (Dense<T>::potrf(hs, k, S, work, lwork, info) != CUSOLVER_STATUS_SUCCESS) return FE_ECUDA;
+        if (read_info() != 0) return FE_EBREAKDOWN;
+        passes = 3;
       }
       // U^T <- R^-T U^T  (U <- U R^-1)
-      if (cublasDtrsm(hb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, k, (int)n,
-                      &one, S, k, U, k) != CUBLAS_STATUS_SUCCESS)
-        return FE_ECUDA;
+      if (Dense<T>::trsm_lt(hb, k, (int)n, S, U) != CUBLAS_STATUS_SUCCESS) return FE_ECUDA;
     }
     return FE_OK;
   }
 
-  // Rayleigh-Ritz on orthonormal *U: W = H~ U, P = U^T W = Q Lambda Q^T,
-  // U <- U Q, W <- W Q; lam (device) ascending, res (device) residual norms.
-  fe_status rayleigh_ritz(double** U) {
-    const double one = 1.0, zero = 0.0;
-    cudaError_t e = scaled(c, true, *U, W, k, 1.0, 0.0, 0.0, s);
+  // Rayleigh-Ritz on the orthonormal U: W = H~ U, P = U^T W = Q Lambda Q^T,
+  // U <- U Q; then W = H~ U again for the residuals (one scaled product costs
+  // 2 k / 441 of the k x k rotation of W it replaces at p = 6).  lam (device)
+  // ascending, res (device, FP64) the residual norms.
+  fe_status rayleigh_ritz() {
+    const bool fp64 = sizeof(T) == 8;
+    cudaError_t e = scaled(c, fp64, U, W, k, 1.0, 0.0, 0.0, s);
     if (e != cudaSuccess) return from_cuda(e);
-    if (cublasDgemm(hb, CUBLAS_OP_N, CUBLAS_OP_T, k, k, (int)n, &one, *U, k, W, k, &zero, S, k) !=
-        CUBLAS_STATUS_SUCCESS)
-      return FE_ECUDA;
-    if (cusolverDnDsyevd(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, S, k, lam, work, lwork, info) !=
-        CUSOLVER_STATUS_SUCCESS)
-      return FE_ECUDA;
-    const int st = read_info();
-    if (st != 0) return st < 0 ? FE_ECUDA : FE_ENONFINITE;
+    fe_status st = gram(U, W);
+    if (st != FE_OK) return st;
+    if (Dense<T>::syevd(hs, k, S, lam, work, lwork, info) != CUSOLVER_STATUS_SUCCESS) return FE_ECUDA;
+    const int inf = read_info();
+    if (inf != 0) return inf < 0 ? FE_ECUDA : FE_ENONFINITE;
     // (U Q)^T = Q^T U^T
-    if (cublasDgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, k, &one, S, k, *U, k, &zero, T, k) !=
-        CUBLAS_STATUS_SUCCESS)
+    if (Dense<T>::gemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, k, S, k, U, k, Tb, k) != CUBLAS_STATUS_SUCCESS)
       return FE_ECUDA;
-    std::swap(*U, T);
-    if (cublasDgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, k, &one, S, k, W, k, &zero, T, k) !=
-        CUBLAS_STATUS_SUCCESS)
-      return FE_ECUDA;
-    std::swap(W, T);
-    residual_partial_kernel<<<dim3((k + 31) / 32, kResRows), dim3(32, 8), 0, s>>>(*U, W, lam, n, k, part);
+    std::swap(U, Tb);
+    e = scaled(c, fp64, U, W, k, 1.0, 0.0, 0.0, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    residual_partial_kernel<T><<<dim3((k + 31) / 32, kResRows), dim3(32, 8), 0, s>>>(U, W, lam, n, k, part);
     residual_final_kernel<<<(k + 127) / 128, 128, 0, s>>>(part, k, kResRows, res);
     return from_cuda(cudaGetLastError());
   }
 
-  // Lanczos on H~ from a random free vector: returns the extreme Ritz values
-  // and the last off-diagonal (|beta_s| + theta_max bounds the spectrum).
-  fe_status lanczos(int steps, unsigned long long seed, double* theta_min, double* theta_max, double* beta_last) {
-    double* v = T;            // v and the previous v in T (n x k holds both for k >= 2), w in W
-    double* w = W;
-    double* vp = T + n;
-    if (k < 2) return FE_EINVAL;
-    random_vector_kernel<<<1024, 256, 0, s>>>(v, n, seed);
-    zero_constrained_kernel<<<1024, 256, 0, s>>>(v, 1, c->mdev, n);
-    cudaError_t e = cudaMemsetAsync(vp, 0, n * sizeof(double), s);
+  // The filter pass of Algorithm 6 on U, with Tb as scratch.
+  fe_status filter_pass(int m, double lmin, double lu, double lmax) {
+    void* x = U;
+    void* y = Tb;
+    cudaError_t e = filter(c, sizeof(T) == 8, &x, &y, k, m, lmin, lu, lmax, s);
     if (e != cudaSuccess) return from_cuda(e);
-    double nv = 0.0;
-    if (cublasDnrm2(hb, (int)n, v, 1, &nv) != CUBLAS_STATUS_SUCCESS || !(nv > 0)) return FE_ECUDA;
-    double inv = 1.0 / nv;
-    cublasDscal(hb, (int)n, &inv, v, 1);
-    std::vector<double> al, be(1, 0.0);
-    double beta = 0.0;
-    for (int j = 0; j < steps; ++j) {
-      e = scaled(c, true, v, w, 1, 1.0, 0.0, 0.0, s);
-      if (e != cudaSuccess) return from_cuda(e);
-      double alpha = 0.0;
-      if (cublasDdot(hb, (int)n, w, 1, v, 1, &alpha) != CUBLAS_STATUS_SUCCESS) return FE_ECUDA;
-      const double ma = -alpha, mb = -beta;
-      cublasDaxpy(hb, (int)n, &ma, v, 1, w, 1);
-      cublasDaxpy(hb, (int)n, &mb, vp, 1, w, 1);
-      if (cublasDnrm2(hb, (int)n, w, 1, &beta) != CUBLAS_STATUS_SUCCESS) return FE_ECUDA;
-      if (!std::isfinite(alpha) || !std::isfinite(beta)) return FE_ENONFINITE;
-      al.push_back(alpha);
-      if (j + 1 < steps) be.push_back(beta);
-      if (beta <= 1e-300) break;
-      // vp <- v, v <- w / beta
-      cublasDcopy(hb, (int)n, v, 1, vp, 1);
-      const double ib = 1.0 / beta;
-      cublasDcopy(hb, (int)n, w, 1, v, 1);
-      cublasDscal(hb, (int)n, &ib, v, 1);
+    if (x != U) std::swap(U, Tb);
+    return from_cuda(cudaGetLastError());
+  }
+
+  fe_status pull(std::vector<double>& hlam, std::vector<double>& hres) {
+    std::vector<T> l(k);
+    cudaError_t e = cudaMemcpyAsync(l.data(), lam, k * sizeof(T), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hres.data(), res, k * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return FE_ECUDA;
+    for (int j = 0; j < k; ++j) {
+      hlam[j] = (double)l[j];
+      if (!std::isfinite(hlam[j]) || !std::isfinite(hres[j])) return FE_ENONFINITE;
     }
-    be.resize(al.size());
-    tridiag_extremes(al, be, theta_min, theta_max);
-    *beta_last = beta;
     return FE_OK;
   }
 };
+
+// Lanczos on H~ from a random free vector (FP64): the extreme Ritz values of
+// the tridiagonal matrix and the last off-diagonal (theta_max + |beta|
+// bounds the spectrum from above).  v, the previous v and w live in the two
+// work blocks (each n x k, k >= 2).
+fe_status lanczos(Chfsi<double>& ch, int steps, unsigned long long seed, double* theta_min, double* theta_max,
+                  double* beta_last) {
+  const size_t n = ch.n;
+  const int ni = (int)n;
+  cublasHandle_t hb = ch.hb;
+  double* v = ch.Tb;
+  double* vp = ch.Tb + n;
+  double* w = ch.W;
+  random_vector_kernel<<<1024, 256, 0, ch.s>>>(v, n, seed);
+  zero_constrained_kernel<<<1024, 256, 0, ch.s>>>(v, 1, ch.c->mdev, n);
+  cudaError_t e = cudaMemsetAsync(vp, 0, n * sizeof(double), ch.s);
+  if (e != cudaSuccess) return from_cuda(e);
+  double nv = 0.0;
+  if (cublasDnrm2(hb, ni, v, 1, &nv) != CUBLAS_STATUS_SUCCESS || !(nv > 0)) return FE_ECUDA;
+  double inv = 1.0 / nv;
+  cublasDscal(hb, ni, &inv, v, 1);
+  std::vector<double> al, be(1, 0.0);
+  double beta = 0.0;
+  for (int j = 0; j < steps; ++j) {
+    e = scaled(ch.c, true, v, w, 1, 1.0, 0.0, 0.0, ch.s);
+    if (e != cudaSuccess) return from_cuda(e);
+    double alpha = 0.0;
+    if (cublasDdot(hb, ni, w, 1, v, 1, &alpha) != CUBLAS_STATUS_SUCCESS) return FE_ECUDA;
+    const double ma = -alpha, mb = -beta;
+    cublasDaxpy(hb, ni, &ma, v, 1, w, 1);
+    cublasDaxpy(hb, ni, &mb, vp, 1, w, 1);
+    if (cublasDnrm2(hb, ni, w, 1, &beta) != CUBLAS_STATUS_SUCCESS) return FE_ECUDA;
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return FE_ENONFINITE;
+    al.push_back(alpha);
+    if (j + 1 < steps) be.push_back(beta);
+    if (beta <= 1e-300) break;
+    cublasDcopy(hb, ni, v, 1, vp, 1);
+    const double ib = 1.0 / beta;
+    cublasDcopy(hb, ni, w, 1, v, 1);
+    cublasDscal(hb, ni, &ib, v, 1);
+  }
+  be.resize(al.size());
+  tridiag_extremes(al, be, theta_min, theta_max);
+  *beta_last = beta;
+  return FE_OK;
+}
 
 }  // namespace
 
@@ -417,30 +513,31 @@ extern "C" fe_status fe_chfsi(fe_ctx* c, double* U, int k, const fe_chfsi_desc* 
       !(d->tol > 0) || (d->filter_mode != FE_FP64 && d->filter_mode != FE_FP32))
     return FE_EINVAL;
   size_t free_dofs = c->n_dofs;
-  if (!c->periodic)
-    free_dofs = (size_t)(c->mdev.Nx - 2) * (c->mdev.Ny - 2) * (c->mdev.Nz - 2);
+  if (!c->periodic) free_dofs = (size_t)(c->mdev.Nx - 2) * (c->mdev.Ny - 2) * (c->mdev.Nz - 2);
   if ((size_t)k > free_dofs) return FE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = ensure_msq(c);
   if (e != cudaSuccess) return from_cuda(e);
-  Chfsi ch;
-  ch.c = c;
-  ch.s = s;
-  ch.n = c->n_dofs;
-  ch.k = k;
-  e = handles(c, s, &ch.hb, &ch.hs);
+  cublasHandle_t hb;
+  cusolverDnHandle_t hs;
+  e = handles(c, s, &hb, &hs);
   if (e != cudaSuccess) return from_cuda(e);
-  cublasSetPointerMode(ch.hb, CUBLAS_POINTER_MODE_HOST);
-  e = ch.alloc();
+  cublasSetPointerMode(hb, CUBLAS_POINTER_MODE_HOST);
+  const bool mixed = d->filter_mode == FE_FP32;
+  Chfsi<double> d64{c, s, hb, hs, c->n_dofs, k};
+  Chfsi<float> d32{c, s, hb, hs, c->n_dofs, k};
+  e = d64.alloc(U);
+  if (e == cudaSuccess && mixed) e = d32.alloc(nullptr);
   if (e != cudaSuccess) {
-    ch.release();
+    d64.release(U);
+    if (mixed) d32.release(nullptr);
     return from_cuda(e);
   }
   cudaEvent_t ev[2];
   cudaEventCreate(&ev[0]);
   cudaEventCreate(&ev[1]);
   fe_chfsi_info inf{};
-  double t_total = 0.0;
+  double t_total = 0.0, t_lz = 0.0;
   auto timed = [&](double* acc, auto&& fn) -> fe_status {
     cudaEventRecord(ev[0], s);
     const fe_status st = fn();
@@ -452,83 +549,68 @@ extern "C" fe_status fe_chfsi(fe_ctx* c, double* U, int k, const fe_chfsi_desc* 
     t_total += ms * 1e-3;
     return st;
   };
-
-  double* Ucur = U;
   std::vector<double> hlam(k), hres(k);
-  fe_status st = FE_OK;
-  double th_min = 0, th_max = 0, beta = 0;
-  double t_lz = 0.0;
-  st = timed(&t_lz, [&] { return ch.lanczos(d->lanczos_steps, d->seed, &th_min, &th_max, &beta); });
-  const double lmax0 = th_max + std::fabs(beta);
-  auto pull = [&]() -> fe_status {
-    cudaError_t e2 = cudaMemcpyAsync(hlam.data(), ch.lam, k * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(hres.data(), ch.res, k * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
-    if (e2 != cudaSuccess) return FE_ECUDA;
-    for (int j = 0; j < k; ++j)
-      if (!std::isfinite(hlam[j]) || !std::isfinite(hres[j])) return FE_ENONFINITE;
-    return FE_OK;
-  };
   auto max_res = [&]() { return *std::max_element(hres.begin(), hres.begin() + d->n_wanted); };
+  double th_min = 0, th_max = 0, beta = 0;
+  fe_status st = timed(&t_lz, [&] { return lanczos(d64, d->lanczos_steps, d->seed, &th_min, &th_max, &beta); });
+  const double lmax0 = th_max + std::fabs(beta);
+  const size_t nk = c->n_dofs * (size_t)k;
+  // Rounds run in FP32 (filter, Cholesky QR, Rayleigh-Ritz) while the mixed
+  // mode's residual is above fp32_switch; the FP64 rounds decide convergence.
+  bool fp32 = mixed;
+  auto round_start = [&]() -> fe_status {   // orthonormalise + project the current block
+    fe_status r = fp32 ? timed(&inf.seconds_orth, [&] { return d32.cholqr(); })
+                       : timed(&inf.seconds_orth, [&] { return d64.cholqr(); });
+    if (r == FE_OK)
+      r = fp32 ? timed(&inf.seconds_rr, [&] { return d32.rayleigh_ritz(); })
+               : timed(&inf.seconds_rr, [&] { return d64.rayleigh_ritz(); });
+    if (r == FE_OK) r = fp32 ? d32.pull(hlam, hres) : d64.pull(hlam, hres);
+    return r;
+  };
   if (st == FE_OK) {
-    zero_constrained_kernel<<<1024, 256, 0, s>>>(Ucur, k, c->mdev, ch.n);
-    st = timed(&inf.seconds_orth, [&] { return ch.cholqr(Ucur); });
+    zero_constrained_kernel<<<1024, 256, 0, s>>>(d64.U, k, c->mdev, c->n_dofs);
+    if (fp32) convert_kernel<double, float><<<2048, 256, 0, s>>>(d64.U, d32.U, nk);
+    st = round_start();
   }
-  if (st == FE_OK) st = timed(&inf.seconds_rr, [&] { return ch.rayleigh_ritz(&Ucur); });
-  if (st == FE_OK) st = pull();
   double lmax = lmax0, lu = 0, lmin = 0;
-  while (st == FE_OK && inf.iterations < d->max_iter && max_res() > d->tol) {
+  while (st == FE_OK) {
+    if (fp32 && max_res() <= std::max(d->fp32_switch, d->tol)) {
+      // switch to FP64: take the FP32 block over and re-project it
+      convert_kernel<float, double><<<2048, 256, 0, s>>>(d32.U, d64.U, nk);
+      fp32 = false;
+      st = round_start();
+      continue;
+    }
+    if (!fp32 && max_res() <= d->tol) break;
+    if (inf.iterations >= d->max_iter) break;
     lu = hlam[k - 1];
     lmin = hlam[0];
     lmax = std::max(lmax0, lu + 1e-3 * std::fabs(lu));
     if (!(lmin < lu)) lmin = lu - 1e-3 * (lmax - lu);
-    const bool fp32 = d->filter_mode == FE_FP32 && max_res() > d->fp32_switch;
-    st = timed(&inf.seconds_filter, [&]() -> fe_status {
-      cudaError_t e2;
-      if (fp32) {
-        // the FP32 pair lives in W (free during the filter): two n x k float blocks
-        float* x32 = reinterpret_cast<float*>(ch.W);
-        float* y32 = x32 + ch.n * (size_t)k;
-        convert_kernel<double, float><<<2048, 256, 0, s>>>(Ucur, x32, ch.n * (size_t)k);
-        void* x = x32;
-        void* y = y32;
-        e2 = filter(c, false, &x, &y, k, d->degree, lmin, lu, lmax, s);
-        if (e2 == cudaSuccess)
-          convert_kernel<float, double><<<2048, 256, 0, s>>>(static_cast<float*>(x), Ucur, ch.n * (size_t)k);
-      } else {
-        void* x = Ucur;
-        void* y = ch.T;
-        e2 = filter(c, true, &x, &y, k, d->degree, lmin, lu, lmax, s);
-        if (e2 == cudaSuccess && x != Ucur) {
-          // the filtered block is in T: take T as the current block
-          ch.T = Ucur;
-          Ucur = static_cast<double*>(x);
-        }
-      }
-      if (e2 == cudaSuccess) e2 = cudaGetLastError();
-      return from_cuda(e2);
-    });
+    st = fp32 ? timed(&inf.seconds_filter, [&] { return d32.filter_pass(d->degree, lmin, lu, lmax); })
+              : timed(&inf.seconds_filter, [&] { return d64.filter_pass(d->degree, lmin, lu, lmax); });
     inf.filter_applies += d->degree;
     if (fp32) inf.fp32_passes++;
-    if (st == FE_OK) st = timed(&inf.seconds_orth, [&] { return ch.cholqr(Ucur); });
-    if (st == FE_OK) st = timed(&inf.seconds_rr, [&] { return ch.rayleigh_ritz(&Ucur); });
-    if (st == FE_OK) st = pull();
     inf.iterations++;
+    if (st == FE_OK) st = round_start();
   }
-  if (Ucur != U) {
-    // the result sits in one of the work blocks: copy it home, and hand the
-    // user's block back to the work set so that release() frees the right ones
-    cudaError_t e2 = cudaMemcpyAsync(U, Ucur, ch.n * (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
-    if (ch.W == U) ch.W = Ucur;
-    else if (ch.T == U) ch.T = Ucur;
+  if (st == FE_OK && fp32) {
+    // max_iter ended an FP32 run: finish with an FP64 projection so that the
+    // reported pairs and residuals are FP64
+    convert_kernel<float, double><<<2048, 256, 0, s>>>(d32.U, d64.U, nk);
+    fp32 = false;
+    st = round_start();
+  }
+  if (d64.U != U) {
+    cudaError_t e2 = cudaMemcpyAsync(U, d64.U, nk * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e2 != cudaSuccess && st == FE_OK) st = FE_ECUDA;
   }
   cudaStreamSynchronize(s);
-  ch.release();
+  d64.release(U);
+  if (mixed) d32.release(nullptr);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
-  if (st == FE_OK || st == FE_ENOTCONV) {
+  if (st == FE_OK) {
     inf.max_residual = max_res();
     for (int j = 0; j < d->n_wanted; ++j) inf.converged += hres[j] <= d->tol;
     if (lambda) std::copy(hlam.begin(), hlam.end(), lambda);

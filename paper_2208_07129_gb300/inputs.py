@@ -159,6 +159,15 @@ WORKLOADS = {
                     "normal", 2, "gauss", v_seed=12),
     "c5": Workload("24^3 unit cube, p=6, n_q=8, Dirichlet-0, 128 right-hand sides", 24, 24, 24, False, 6, 8, 128,
                    "normal", 5, "gauss", v_seed=15, v_amp=0.125, v_shift=1.0),
+    # eigenproblems (Sec. 4.3): n_vec is the subspace size k of the filtered subspace iteration
+    "e0": Workload("unit cube 8^3, p=6, n_q=8, Dirichlet-0: 100 smallest eigenpairs, 128-vector subspace, "
+                   "Chebyshev degree 40, residual 5e-5", 8, 8, 8, False, 6, 8, 128, "normal", 7, "gauss", v_seed=17,
+                   extra={"n_wanted": 100, "degree": 40, "tol": 5e-5}),
+    # the size of the paper's GPU eigen case for FEOrder 6 (1,092,727 DoFs, 1024 wanted + 25 % buffer,
+    # Chebyshev degree 67)
+    "e1": Workload("unit cube 17^3, p=6, n_q=8, Dirichlet-0 (1,092,727 DoFs): 1024 wanted eigenpairs, "
+                   "1280-vector subspace, Chebyshev degree 67", 17, 17, 17, False, 6, 8, 1280, "normal", 8, "gauss",
+                   v_seed=18, extra={"n_wanted": 1024, "degree": 67, "tol": 5e-5}),
 }
 
 
