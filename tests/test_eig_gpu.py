@@ -175,3 +175,42 @@ def test_chfsi_reports_nonconvergence(fe):
         assert np.all(np.isfinite(res["eigenvalues"]))
     finally:
         fe.fe_destroy(ctx)
+
+
+def test_scaled_product_full_size(fe):
+    """The paper-size eigen case in the filter's launch configuration (17^3,
+    p = 6, k = 1280): sampled rows of the GLL mass equal the oracle's (a row
+    of the GLL-assembled overlap matrix times a vector of ones), and the
+    fused product equals its composition a M^-1/2 A (M^-1/2 X) + b X + c Y
+    from fe_apply, a property that holds at any size."""
+    w = inputs.WORKLOADS["e1"]
+    ctx = fe.setup_workload(w)
+    try:
+        n, k, p = w.num_dofs, w.n_vec, w.p
+        m = fe.fe_mass_gll(ctx)
+        mesh = orc.Mesh(w.nx, w.ny, w.nz, periodic=w.periodic)
+        mask = w.boundary_mask()
+        rng = np.random.default_rng(5)
+        rows = np.unique(np.concatenate([rng.integers(0, n, 64), [0, n - 1, n // 2]]))
+        mref = orc.apply_rows(mesh, p, p + 1, np.ones((n, 1)), rows, kind=orc.GLL, mu=0.0,
+                              Vq=np.ones((w.num_cells, (p + 1) ** 3)), constrain=False)[:, 0]
+        mref[mask[rows]] = 1.0
+        np.testing.assert_allclose(m[rows], mref, rtol=1e-13, atol=0)
+
+        g = torch.Generator(device="cuda")
+        g.manual_seed(3)
+        X = torch.randn(n, k, device="cuda", dtype=torch.float64, generator=g)
+        Y = torch.randn(n, k, device="cuda", dtype=torch.float64, generator=g)
+        Y0 = Y.clone()
+        a, b, c = 0.3, -0.7, 0.2
+        fe.fe_apply_scaled(ctx, X, Y, a, b, c)
+        msq = torch.from_numpy(1.0 / np.sqrt(m)).cuda()[:, None]
+        Xs = X * msq
+        AXs = torch.empty_like(X)
+        fe.fe_apply(ctx, Xs, AXs)
+        ref = a * msq * AXs + b * X + c * Y0
+        ref[torch.from_numpy(mask).cuda()] = 0.0
+        rel = (torch.linalg.norm(Y - ref) / torch.linalg.norm(ref)).item()
+        assert rel <= 1e-12, rel
+    finally:
+        fe.fe_destroy(ctx)
