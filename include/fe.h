@@ -127,7 +127,7 @@ fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream)
  * per CTA (1..256; CTAs are capped at 256 threads), and the variant
  * (FE_FP64: 0 = line kernel with even-odd contractions, 1 = plain line
  * kernel; FE_FP32: 0 or 1 = line kernel, 2 = register-plane kernel, n_q <= 8
- * only).
+ * only, 3 = line kernel with even-odd contractions).
  * FE_EUNSUPPORTED for the tensor-core modes, whose tile is fixed.  Applies to
  * later fe_apply calls. */
 fe_status fe_set_tile(fe_ctx* ctx, fe_mode mode, int vectors_per_cta, int lines, int variant);

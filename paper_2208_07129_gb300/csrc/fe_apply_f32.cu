@@ -1,6 +1,8 @@
-// FP32 CUDA-core instantiations: the line kernel, or the register-plane
-// kernel (n_q <= 8) when selected with fe_set_tile.
+// FP32 CUDA-core instantiations: the line kernel, the line kernel with
+// even-odd contractions, or the register-plane kernel (n_q <= 8), as
+// selected with fe_set_tile.
 #include "fe_dispatch.cuh"
+#include "fe_evenodd.cuh"
 #include "fe_plane_kernel.cuh"
 
 namespace fe {
@@ -11,6 +13,7 @@ cudaError_t pick(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStrea
   if constexpr (NQ <= 8) {
     if (c->fp32_variant == 2) return launch_plane<NP, NQ, GEN>(c, X, Y, n_vec, s);
   }
+  if (c->fp32_variant == 3) return launch_apply_eo<float, NP, NQ, GEN>(c, X, Y, n_vec, s, c->vb32, c->nty32);
   return launch_apply<float, NP, NQ, GEN>(c, X, Y, n_vec, s, c->vb32, c->nty32);
 }
 }  // namespace

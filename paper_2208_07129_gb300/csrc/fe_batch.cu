@@ -8,8 +8,9 @@
 // from the queue earlier by running CTAs, so the wait always ends (and it is
 // bounded besides: a CTA that gives up records FE_ETIMEOUT).  Within a colour
 // the cells share no node, so assembly stays conflict-free and the result is
-// bitwise the one of the per-problem launches (Sec. 3.1.2: all cells and
-// batches of vectors evaluated concurrently, here across problems too).
+// bitwise the one of the per-problem launches of the even-odd line kernel
+// (the same cell body; Sec. 3.1.2: all cells and batches of vectors evaluated
+// concurrently, here across problems too).
 //
 // Each problem gets its own tile (vectors per item x lines per CTA, 128
 // threads) from a small autotuner that times the candidate tiles on a proxy
@@ -24,12 +25,14 @@
 #include "fe_internal.h"
 #include "fe_cell_kernel.cuh"
 #include "fe_dispatch.cuh"
+#include "fe_evenodd.cuh"
 #include "../../include/fe_batch.h"
 
 namespace fe {
 
 constexpr int kBatchThreads = 128;
 constexpr int kMaxColors = 27;
+constexpr int kTabImage = 256;   // elements of an EOTables<T, NP, NQ> image (195 at p = 8, n_q = 10)
 
 template <typename T>
 struct BatchProblemDev {
@@ -37,7 +40,7 @@ struct BatchProblemDev {
   Geom<T> geo;
   int n_vec, vb, nty, kind, n_vb;
   const int* cells;                                    // colour-sorted cell ids
-  T tab[kMaxNQ * (kMaxP + 1) + kMaxNQ * kMaxNQ];       // Tables<T, NP, NQ> image (N then D)
+  T tab[kTabImage];                                    // EOTables<T, NP, NQ> image
 };
 
 struct WorkItem {
@@ -50,12 +53,12 @@ constexpr int kind_of(int p) { return p - 3; }
 template <typename T, int NP, int NQ>
 __device__ __forceinline__ void run_item(const BatchProblemDev<T>& P, const WorkItem& w, const T* X, T* Y, T* smem,
                                          const T* stab) {
-  const Tables<T, NP, NQ>& tab = *reinterpret_cast<const Tables<T, NP, NQ>*>(stab);
+  const EOTables<T, NP, NQ>& tab = *reinterpret_cast<const EOTables<T, NP, NQ>*>(stab);
   const int tid = threadIdx.x, vb = P.vb;
   const int v = tid % vb, ty = tid / vb, nty = kBatchThreads / vb;
   for (int c = 0; c < w.cell_count; ++c) {
     const int e = P.cells[w.cell_begin + c];
-    cell_body<T, NP, NQ, false>(tab, P.m, P.geo, e, w.vb, vb, v, ty, nty, P.n_vec, X, Y, smem);
+    cell_body_eo<T, NP, NQ, false>(tab, P.m, P.geo, e, w.vb, vb, v, ty, nty, P.n_vec, X, Y, smem);
     __syncthreads();
   }
 }
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchProblem
                                                              int* next, int* done, const int* __restrict__ need,
                                                              int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(16) T stab[kMaxNQ * (kMaxP + 1) + kMaxNQ * kMaxNQ];
+  __shared__ __align__(16) T stab[kTabImage];
   __shared__ int s_item;
   T* smem = reinterpret_cast<T*>(smem_raw);
   for (;;) {
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchProblem
       }
       __threadfence();
     }
-    for (int k = threadIdx.x; k < kMaxNQ * (kMaxP + 1) + kMaxNQ * kMaxNQ; k += blockDim.x) stab[k] = P.tab[k];
+    for (int k = threadIdx.x; k < kTabImage; k += blockDim.x) stab[k] = P.tab[k];
     __syncthreads();
     const T* X = static_cast<const T*>(ptrs[2 * w.problem]);
     T* Y = static_cast<T*>(const_cast<void*>(ptrs[2 * w.problem + 1]));
@@ -142,6 +145,14 @@ fe_status from_cuda(cudaError_t e) {
 template <typename T>
 size_t tile_smem(int nq, int vb) { return (size_t)3 * nq * nq * nq * vb * sizeof(T); }
 
+// The even-odd tables of one problem, copied into its table image.
+template <typename T, int NP, int NQ>
+void eo_image(const fe_ctx* c, T* img) {
+  static_assert(sizeof(EOTables<T, NP, NQ>) <= kTabImage * sizeof(T), "table image too small");
+  const EOTables<T, NP, NQ> t = make_eotables<T, NP, NQ>(c);
+  std::memcpy(img, &t, sizeof(t));
+}
+
 // Candidate vectors-per-CTA of the autotuner for one problem.
 std::vector<int> candidates(int nq, int n_vec, size_t elem) {
   std::vector<int> out;
@@ -154,14 +165,18 @@ std::vector<int> candidates(int nq, int n_vec, size_t elem) {
   return out;
 }
 
-// Time one apply of a 4^3 periodic proxy with the problem's degree and block
-// width for every candidate tile; return the fastest vectors-per-CTA.
-int autotune(const fe_ctx* c, int n_vec, fe_mode mode, float* spent_ms) {
+// Time one apply of an 8^3 periodic proxy (64 cells per colour: enough CTAs
+// to fill the GPU at every candidate, unlike a tiny mesh, which rewards the
+// narrowest tile for its parallelism alone) with the problem's degree and
+// block width (capped at 64 vectors) for every candidate tile; return the
+// fastest vectors-per-CTA.
+int autotune(const fe_ctx* c, int n_vec_full, fe_mode mode, float* spent_ms) {
   const size_t elem = mode == FE_FP64 ? 8 : 4;
-  std::vector<int> cand = candidates(c->nq, n_vec, elem);
+  std::vector<int> cand = candidates(c->nq, n_vec_full, elem);
   if (cand.size() == 1) return cand[0];
+  const int n_vec = std::min(n_vec_full, 64);
   fe_mesh_desc md{};
-  md.nx = md.ny = md.nz = 4;
+  md.nx = md.ny = md.nz = 8;
   md.hi[0] = md.hi[1] = md.hi[2] = 1.0;
   md.bc = FE_BC_PERIODIC;
   fe_quad_desc qd{c->nq, c->quad_kind};
@@ -178,7 +193,7 @@ int autotune(const fe_ctx* c, int n_vec, fe_mode mode, float* spent_ms) {
     cudaEventCreate(&b);
     float best_ms = 1e30f;
     for (int vb : cand) {
-      fe_set_tile(px, mode, vb, kBatchThreads / vb, 1);
+      fe_set_tile(px, mode, vb, kBatchThreads / vb, mode == FE_FP64 ? 0 : 3);   // the even-odd line kernel
       fe_apply(px, X, Y, n_vec, nullptr);
       cudaEventRecord(a);
       for (int r = 0; r < 3; ++r) fe_apply(px, X, Y, n_vec, nullptr);
@@ -234,9 +249,14 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
     P.n_vb = (P.n_vec + vb - 1) / vb;
     b->vb[i] = vb;
     std::memset(P.tab, 0, sizeof(P.tab));
-    for (int q = 0; q < c->nq; ++q) {
-      for (int k = 0; k < c->np; ++k) P.tab[q * c->np + k] = (T)c->Nf[q * c->np + k];
-      for (int k = 0; k < c->nq; ++k) P.tab[c->nq * c->np + q * c->nq + k] = (T)c->Df[q * c->nq + k];
+    switch (P.kind) {
+      case 0: eo_image<T, 4, 5>(c, P.tab); break;
+      case 1: eo_image<T, 5, 6>(c, P.tab); break;
+      case 2: eo_image<T, 6, 7>(c, P.tab); break;
+      case 3: eo_image<T, 7, 8>(c, P.tab); break;
+      case 4: eo_image<T, 8, 9>(c, P.tab); break;
+      case 5: eo_image<T, 9, 10>(c, P.tab); break;
+      default: break;
     }
     smem = std::max(smem, tile_smem<T>(c->nq, vb));
   }

@@ -129,7 +129,7 @@ struct fe_ctx {
   void* solver = nullptr;
   // launch shape per mode (vectors per CTA, lines per CTA)
   int vb64 = 8, nty64 = 16, vb32 = 8, nty32 = 32;
-  int fp32_variant = 0;   // 0 / 1: line kernel, 2: register-plane kernel
+  int fp32_variant = 0;   // 0 / 1: line kernel, 2: register-plane kernel, 3: even-odd line kernel
   int fp64_variant = 0;   // 0: even-odd line kernel, 1: plain line kernel
 };
 

@@ -244,8 +244,11 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
   c->periodic = mesh->bc == FE_BC_PERIODIC;
   c->p = p; c->np = p + 1; c->nq = quad->n_q; c->quad_kind = quad->kind; c->mu = mu;
   c->general = mesh->vertex_xyz != nullptr;
-  // FP64 tile measured on GB300: 8 vectors x 16 lines up to n_q = 8, 4 x 32 above
-  if (quad->n_q >= 9) { c->vb64 = 4; c->nty64 = 32; }
+  // FP64 tile measured on GB300: 8 vectors x 16 lines up to n_q = 8, 4 x 32 above;
+  // FP32: even-odd line kernel, 8 x 32 up to n_q = 8, 4 x 64 above (two more
+  // CTAs per SM in the 48 KB of shared memory that 4 vectors of n_q = 10 take)
+  c->fp32_variant = 3;
+  if (quad->n_q >= 9) { c->vb64 = 4; c->nty64 = 32; c->vb32 = 4; c->nty32 = 64; }
   const int np = c->np, nq = c->nq;
   const int add = c->periodic ? 0 : 1;
   c->mdev.nx = c->nx; c->mdev.ny = c->ny; c->mdev.nz = c->nz;
@@ -428,10 +431,10 @@ extern "C" fe_mode fe_get_mode(const fe_ctx* c) { return c ? c->mode : FE_FP64; 
 
 extern "C" fe_status fe_set_tile(fe_ctx* c, fe_mode mode, int vectors_per_cta, int lines, int variant) {
   if (!c || vectors_per_cta < 1 || vectors_per_cta > 32 || (vectors_per_cta & (vectors_per_cta - 1)) != 0 ||
-      lines < 1 || lines > 256 || variant < 0 || variant > 2)
+      lines < 1 || lines > 256 || variant < 0 || variant > 3)
     return FE_EINVAL;
   if (mode == FE_FP64) {
-    if (variant == 2) return FE_EINVAL;
+    if (variant >= 2) return FE_EINVAL;
     c->vb64 = vectors_per_cta;
     c->nty64 = lines;
     c->fp64_variant = variant;

@@ -38,9 +38,7 @@ def test_batch_matches_per_problem(fe, mode, autotune):
             X = torch.from_numpy(w.make_x()).to(device="cuda", dtype=dt)
             Xs.append(X)
             Ys.append(torch.full_like(X, float("nan")))
-            fe.fe_set_mode(ctx, mode)
-            if mode == "fp64":
-                fe.fe_set_tile(ctx, "fp64", 8, 16, 1)   # the plain line kernel, whose cell body the batch runs
+            fe.fe_set_mode(ctx, mode)   # default kernel: the even-odd line kernel, whose cell body the batch runs
             Y = torch.empty_like(X)
             fe.fe_apply(ctx, X, Y)
             Yref.append(Y)
