@@ -63,9 +63,14 @@ typedef enum { FE_QUAD_GAUSS = 0, FE_QUAD_GLL = 1 } fe_quad_kind;
  * operation stays FP32.  FE_TF32X3: as FE_TF32, but every operand is split
  * into hi + lo TF32 parts and each product is accumulated as
  * lo*hi + hi*lo + hi*hi (three tensor-core products; the split-TF32 scheme of
- * Ootomo and Yokota, 2022), which restores FP32-level accuracy.  Geometry is
- * always computed in FP64. */
-typedef enum { FE_FP64 = 0, FE_FP32 = 1, FE_TF32 = 2, FE_BF16 = 3, FE_TF32X3 = 4 } fe_mode;
+ * Ootomo and Yokota, 2022), which restores FP32-level accuracy.  FE_DF64:
+ * double data; the cell kernel computes in double-float arithmetic (each
+ * value an unevaluated sum of two floats, ~48 significant bits; error-free
+ * sums and products, compensated dot products) on the FP32 pipe, which
+ * GB300 runs at 64 times its FP64 rate; errors stay within the FP64 bound
+ * (1e-12 relative).
+ * Geometry is always computed in FP64. */
+typedef enum { FE_FP64 = 0, FE_FP32 = 1, FE_TF32 = 2, FE_BF16 = 3, FE_TF32X3 = 4, FE_DF64 = 5 } fe_mode;
 
 typedef struct {
   int nx, ny, nz;          /* cells per direction, >= 1 (>= 2 when periodic) */
@@ -127,7 +132,8 @@ fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream)
  * per CTA (1..256; CTAs are capped at 256 threads), and the variant
  * (FE_FP64: 0 = line kernel with even-odd contractions, 1 = plain line
  * kernel; FE_FP32: 0 or 1 = line kernel, 2 = register-plane kernel, n_q <= 8
- * only, 3 = line kernel with even-odd contractions).
+ * only, 3 = line kernel with even-odd contractions; FE_DF64: 0, the
+ * double-float even-odd line kernel).
  * FE_EUNSUPPORTED for the tensor-core modes, whose tile is fixed.  Applies to
  * later fe_apply calls. */
 fe_status fe_set_tile(fe_ctx* ctx, fe_mode mode, int vectors_per_cta, int lines, int variant);

@@ -36,8 +36,9 @@ fe_status fe_mass_gll(fe_ctx* ctx, double* m_host);
  * with the M^-1/2 scalings folded into the gather and the scatter and the
  * b X + c Y terms into the first write of each node (colour-ordered
  * assembly), so the product costs one pass over X and Y like fe_apply.
- * Mode FE_FP64 (even-odd cell kernel) or FE_FP32 (line kernel); the
- * tensor-core modes return FE_EUNSUPPORTED.  X and Y must not overlap.  Y is
+ * Mode FE_FP64 (even-odd cell kernel), FE_DF64 (FP64 data, double-float
+ * arithmetic) or FE_FP32 (even-odd line kernel in FP32); the tensor-core
+ * modes return FE_EUNSUPPORTED.  X and Y must not overlap.  Y is
  * read only when c != 0 (it may be uninitialised when c == 0).  Constrained
  * rows of Y are written 0. */
 fe_status fe_apply_scaled(fe_ctx* ctx, const void* X, void* Y, int n_vec, double a, double b, double c,
@@ -48,7 +49,8 @@ fe_status fe_apply_scaled(fe_ctx* ctx, const void* X, void* Y, int n_vec, double
  * lambda_min (scaled three-term recurrence; sigma is updated after every
  * step).  m scaled products; the block ends in X, Y is scratch of the same
  * size.  Requires lambda_min < lambda_u < lambda_max (else FE_EINVAL) and
- * degree >= 1.  Element type per the context's mode (FE_FP64 or FE_FP32). */
+ * degree >= 1.  Element type per the context's mode (FE_FP64, FE_DF64 or
+ * FE_FP32). */
 fe_status fe_chebyshev_filter(fe_ctx* ctx, void* X, void* Y, int n_vec, int degree, double lambda_min,
                               double lambda_u, double lambda_max, void* stream);
 
@@ -58,8 +60,14 @@ typedef struct {
   double tol;          /* stop when max_{j < n_wanted} ||H~ u_j - lambda_j u_j||_2 <= tol */
   int max_iter;        /* filter + orthonormalise + Rayleigh-Ritz rounds, >= 1 */
   int lanczos_steps;   /* Lanczos steps bounding the spectrum (upper bound of H~), >= 2 */
-  int filter_mode;     /* FE_FP64, or FE_FP32: FP32 filter passes while the residual is above fp32_switch */
-  double fp32_switch;  /* residual below which an FE_FP32 run filters in FP64 */
+  int filter_mode;     /* arithmetic of the scaled products (filter, projection, Lanczos):
+                          FE_FP64: FP64 throughout;
+                          FE_DF64: FP64 data, double-float products (FE_DF64 of fe.h);
+                          FE_FP32: whole rounds (filter, Cholesky QR, Rayleigh-Ritz) in FP32 while the
+                          wanted residual is above fp32_switch, then FP64 rounds with double-float
+                          products.  FP64 rounds always decide convergence. */
+  double fp32_switch;  /* residual below which an FE_FP32 run switches to FP64 rounds; keep it above
+                          ~1e-6 x the largest wanted eigenvalue (the FP32 residual floor) */
   unsigned long long seed;  /* Lanczos start vector */
 } fe_chfsi_desc;
 
@@ -88,10 +96,10 @@ typedef struct {
  * largest and smallest current Ritz values), orthonormalises it (Cholesky QR,
  * twice, with a diagonal shift if the Gram matrix is not numerically
  * positive definite), and projects: W = H~ U, P = U^T W, P = Q Lambda Q^T,
- * U <- U Q, W <- W Q, residuals from W - U Lambda.  The dense steps use
- * cuBLAS (Gram matrices, rotations) and cuSOLVER (Cholesky, the k x k
- * symmetric eigensolver).
- * Workspace: three more num_dofs x k FP64 blocks (two FP32 blocks when
+ * U <- U Q, then W = H~ U again and the residuals from W - U Lambda.  The
+ * dense steps use cuBLAS (Gram matrices, rotations, triangular solves) and
+ * cuSOLVER (Cholesky, the k x k symmetric eigensolver).
+ * Workspace: two more num_dofs x k FP64 blocks (and three FP32 blocks when
  * filter_mode is FE_FP32), allocated for the call.  Synchronous: returns
  * when the results are on the host.  FE_ENOTCONV if max_iter rounds end
  * above tol (U, lambda, residual still filled); FE_ENONFINITE on a

@@ -9,7 +9,7 @@ namespace {
 fe_status from_cuda(cudaError_t e) {
   return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
 }
-size_t elem_size(fe_mode m) { return m == FE_FP64 ? sizeof(double) : sizeof(float); }
+size_t elem_size(fe_mode m) { return (m == FE_FP64 || m == FE_DF64) ? sizeof(double) : sizeof(float); }
 
 bool overlaps(const void* a, const void* b, size_t bytes) {
   const char* x = static_cast<const char*>(a);
@@ -28,6 +28,7 @@ extern "C" fe_status fe_apply(fe_ctx* c, const void* X, void* Y, int n_vec, void
   cudaError_t e;
   switch (c->mode) {
     case FE_FP64: e = apply_cc_f64(c, static_cast<const double*>(X), static_cast<double*>(Y), n_vec, s); break;
+    case FE_DF64: e = apply_df64(c, static_cast<const double*>(X), static_cast<double*>(Y), n_vec, s); break;
     case FE_FP32: e = apply_cc_f32(c, static_cast<const float*>(X), static_cast<float*>(Y), n_vec, s); break;
     case FE_TF32:
     case FE_BF16:

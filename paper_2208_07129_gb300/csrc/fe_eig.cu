@@ -56,11 +56,17 @@ cudaError_t ensure_msq(fe_ctx* c) {
   return e;
 }
 
-// Y = a H~ X + b X + c Y in FP64 or FP32 (no argument checks).
-cudaError_t scaled(fe_ctx* c, bool fp64, const void* X, void* Y, int n_vec, double a, double b, double cc,
+// Arithmetic of a scaled product: FP32 data and arithmetic, FP64, or FP64
+// data with double-float arithmetic.
+enum Prec { kF32 = 0, kF64 = 1, kDF64 = 2 };
+
+// Y = a H~ X + b X + c Y (no argument checks).
+cudaError_t scaled(fe_ctx* c, int prec, const void* X, void* Y, int n_vec, double a, double b, double cc,
                    cudaStream_t s) {
-  if (fp64) {
+  if (prec != kF32) {
     const Scale<double> sc{c->d_msq64, a, b, cc};
+    if (prec == kDF64)
+      return apply_scaled_df64(c, static_cast<const double*>(X), static_cast<double*>(Y), n_vec, sc, s);
     return apply_scaled_f64(c, static_cast<const double*>(X), static_cast<double*>(Y), n_vec, sc, s);
   }
   const Scale<float> sc{c->d_msq32, (float)a, (float)b, (float)cc};
@@ -69,19 +75,19 @@ cudaError_t scaled(fe_ctx* c, bool fp64, const void* X, void* Y, int n_vec, doub
 
 // The filter loop of Algorithm 6 (sigma updated after every step).  The
 // result is left in *X (the two buffer pointers are swapped as needed).
-cudaError_t filter(fe_ctx* c, bool fp64, void** X, void** Y, int n_vec, int m, double lmin, double lu, double lmax,
+cudaError_t filter(fe_ctx* c, int prec, void** X, void** Y, int n_vec, int m, double lmin, double lu, double lmax,
                    cudaStream_t s) {
   const double e = (lmax - lu) / 2.0, cen = (lmax + lu) / 2.0;
   double sigma = e / (lmin - cen);
   const double sigma1 = sigma, gamma = 2.0 / sigma1;
   double alpha1 = sigma1 / e, alpha2 = -cen;
-  cudaError_t err = scaled(c, fp64, *X, *Y, n_vec, alpha1, alpha1 * alpha2, 0.0, s);
+  cudaError_t err = scaled(c, prec, *X, *Y, n_vec, alpha1, alpha1 * alpha2, 0.0, s);
   for (int d = 2; d <= m && err == cudaSuccess; ++d) {
     const double sigma2 = 1.0 / (gamma - sigma);
     alpha1 = 2.0 * sigma2 / e;
     alpha2 = -sigma * sigma2;
     // X <- alpha1 H~ Y - c alpha1 Y + alpha2 X, then swap(X, Y)
-    err = scaled(c, fp64, *Y, *X, n_vec, alpha1, -cen * alpha1, alpha2, s);
+    err = scaled(c, prec, *Y, *X, n_vec, alpha1, -cen * alpha1, alpha2, s);
     std::swap(*X, *Y);
     sigma = sigma2;
   }
@@ -288,6 +294,7 @@ struct Chfsi {
   int* info = nullptr;
   int lwork = 0;
   bool owns_u = false;
+  int prec = sizeof(T) == 8 ? kF64 : kF32;   // arithmetic of the scaled products
 
   // U: the caller's block (FP64) or nullptr to allocate one (FP32).
   cudaError_t alloc(T* user) {
@@ -363,8 +370,7 @@ struct Chfsi {
   // 2 k / 441 of the k x k rotation of W it replaces at p = 6).  lam (device)
   // ascending, res (device, FP64) the residual norms.
   fe_status rayleigh_ritz() {
-    const bool fp64 = sizeof(T) == 8;
-    cudaError_t e = scaled(c, fp64, U, W, k, 1.0, 0.0, 0.0, s);
+    cudaError_t e = scaled(c, prec, U, W, k, 1.0, 0.0, 0.0, s);
     if (e != cudaSuccess) return from_cuda(e);
     fe_status st = gram(U, W);
     if (st != FE_OK) return st;
@@ -375,7 +381,7 @@ struct Chfsi {
     if (Dense<T>::gemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, k, S, k, U, k, Tb, k) != CUBLAS_STATUS_SUCCESS)
       return FE_ECUDA;
     std::swap(U, Tb);
-    e = scaled(c, fp64, U, W, k, 1.0, 0.0, 0.0, s);
+    e = scaled(c, prec, U, W, k, 1.0, 0.0, 0.0, s);
     if (e != cudaSuccess) return from_cuda(e);
     residual_partial_kernel<T><<<dim3((k + 31) / 32, kResRows), dim3(32, 8), 0, s>>>(U, W, lam, n, k, part);
     residual_final_kernel<<<(k + 127) / 128, 128, 0, s>>>(part, k, kResRows, res);
@@ -386,7 +392,7 @@ struct Chfsi {
   fe_status filter_pass(int m, double lmin, double lu, double lmax) {
     void* x = U;
     void* y = Tb;
-    cudaError_t e = filter(c, sizeof(T) == 8, &x, &y, k, m, lmin, lu, lmax, s);
+    cudaError_t e = filter(c, prec, &x, &y, k, m, lmin, lu, lmax, s);
     if (e != cudaSuccess) return from_cuda(e);
     if (x != U) std::swap(U, Tb);
     return from_cuda(cudaGetLastError());
@@ -429,7 +435,7 @@ fe_status lanczos(Chfsi<double>& ch, int steps, unsigned long long seed, double*
   std::vector<double> al, be(1, 0.0);
   double beta = 0.0;
   for (int j = 0; j < steps; ++j) {
-    e = scaled(ch.c, true, v, w, 1, 1.0, 0.0, 0.0, ch.s);
+    e = scaled(ch.c, ch.prec, v, w, 1, 1.0, 0.0, 0.0, ch.s);
     if (e != cudaSuccess) return from_cuda(e);
     double alpha = 0.0;
     if (cublasDdot(hb, ni, w, 1, v, 1, &alpha) != CUBLAS_STATUS_SUCCESS) return FE_ECUDA;
@@ -479,12 +485,12 @@ extern "C" fe_status fe_apply_scaled(fe_ctx* c, const void* X, void* Y, int n_ve
   if (!c || n_vec < 0) return FE_EINVAL;
   if (n_vec == 0) return FE_OK;
   if (!X || !Y || !std::isfinite(a) || !std::isfinite(b) || !std::isfinite(cc)) return FE_EINVAL;
-  if (c->mode != FE_FP64 && c->mode != FE_FP32) return FE_EUNSUPPORTED;
-  const bool fp64 = c->mode == FE_FP64;
-  if (overlaps(X, Y, c->n_dofs * (size_t)n_vec * (fp64 ? 8 : 4))) return FE_EINVAL;
+  if (c->mode != FE_FP64 && c->mode != FE_FP32 && c->mode != FE_DF64) return FE_EUNSUPPORTED;
+  const int prec = c->mode == FE_FP64 ? kF64 : (c->mode == FE_DF64 ? kDF64 : kF32);
+  if (overlaps(X, Y, c->n_dofs * (size_t)n_vec * (prec != kF32 ? 8 : 4))) return FE_EINVAL;
   cudaError_t e = ensure_msq(c);
   if (e != cudaSuccess) return from_cuda(e);
-  return from_cuda(scaled(c, fp64, X, Y, n_vec, a, b, cc, static_cast<cudaStream_t>(stream)));
+  return from_cuda(scaled(c, prec, X, Y, n_vec, a, b, cc, static_cast<cudaStream_t>(stream)));
 }
 
 extern "C" fe_status fe_chebyshev_filter(fe_ctx* c, void* X, void* Y, int n_vec, int degree, double lmin, double lu,
@@ -492,16 +498,16 @@ extern "C" fe_status fe_chebyshev_filter(fe_ctx* c, void* X, void* Y, int n_vec,
   if (!c || n_vec < 0 || degree < 1) return FE_EINVAL;
   if (n_vec == 0) return FE_OK;
   if (!X || !Y || !(lmin < lu && lu < lmax) || !std::isfinite(lmin) || !std::isfinite(lmax)) return FE_EINVAL;
-  if (c->mode != FE_FP64 && c->mode != FE_FP32) return FE_EUNSUPPORTED;
-  const bool fp64 = c->mode == FE_FP64;
-  const size_t bytes = c->n_dofs * (size_t)n_vec * (fp64 ? 8 : 4);
+  if (c->mode != FE_FP64 && c->mode != FE_FP32 && c->mode != FE_DF64) return FE_EUNSUPPORTED;
+  const int prec = c->mode == FE_FP64 ? kF64 : (c->mode == FE_DF64 ? kDF64 : kF32);
+  const size_t bytes = c->n_dofs * (size_t)n_vec * (prec != kF32 ? 8 : 4);
   if (overlaps(X, Y, bytes)) return FE_EINVAL;
   cudaError_t e = ensure_msq(c);
   if (e != cudaSuccess) return from_cuda(e);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* x = X;
   void* y = Y;
-  e = filter(c, fp64, &x, &y, n_vec, degree, lmin, lu, lmax, s);
+  e = filter(c, prec, &x, &y, n_vec, degree, lmin, lu, lmax, s);
   if (e == cudaSuccess && x != X) e = cudaMemcpyAsync(X, x, bytes, cudaMemcpyDeviceToDevice, s);
   return from_cuda(e);
 }
@@ -510,7 +516,7 @@ extern "C" fe_status fe_chfsi(fe_ctx* c, double* U, int k, const fe_chfsi_desc* 
                               fe_chfsi_info* info, void* stream) {
   if (!c || !U || !d) return FE_EINVAL;
   if (k < 2 || d->n_wanted < 1 || d->n_wanted > k || d->degree < 1 || d->max_iter < 1 || d->lanczos_steps < 2 ||
-      !(d->tol > 0) || (d->filter_mode != FE_FP64 && d->filter_mode != FE_FP32))
+      !(d->tol > 0) || (d->filter_mode != FE_FP64 && d->filter_mode != FE_FP32 && d->filter_mode != FE_DF64))
     return FE_EINVAL;
   size_t free_dofs = c->n_dofs;
   if (!c->periodic) free_dofs = (size_t)(c->mdev.Nx - 2) * (c->mdev.Ny - 2) * (c->mdev.Nz - 2);
@@ -526,6 +532,8 @@ extern "C" fe_status fe_chfsi(fe_ctx* c, double* U, int k, const fe_chfsi_desc* 
   const bool mixed = d->filter_mode == FE_FP32;
   Chfsi<double> d64{c, s, hb, hs, c->n_dofs, k};
   Chfsi<float> d32{c, s, hb, hs, c->n_dofs, k};
+  // FP64-data products in double-float arithmetic unless plain FP64 is asked for
+  d64.prec = d->filter_mode == FE_FP64 ? kF64 : kDF64;
   e = d64.alloc(U);
   if (e == cudaSuccess && mixed) e = d32.alloc(nullptr);
   if (e != cudaSuccess) {

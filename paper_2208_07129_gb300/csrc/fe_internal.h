@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/fe.h"
+#include "fe_ff.cuh"
 
 namespace fe {
 
@@ -108,6 +109,7 @@ struct fe_ctx {
   int* d_cells = nullptr;
   double *d_cellG64 = nullptr, *d_ptG64 = nullptr, *d_ptC64 = nullptr;
   float *d_cellG32 = nullptr, *d_ptG32 = nullptr, *d_ptC32 = nullptr;
+  fe::ff *d_cellGff = nullptr, *d_ptGff = nullptr, *d_ptCff = nullptr;   // double-float copies
   double* d_detJ = nullptr;
   int* d_status = nullptr;
   // staging for fe_apply_host, and the copy streams and events of its
@@ -128,7 +130,7 @@ struct fe_ctx {
   void* blas = nullptr;
   void* solver = nullptr;
   // launch shape per mode (vectors per CTA, lines per CTA)
-  int vb64 = 8, nty64 = 16, vb32 = 8, nty32 = 32;
+  int vb64 = 8, nty64 = 16, vb32 = 8, nty32 = 32, vbdf = 8, ntydf = 32;
   int fp32_variant = 0;   // 0 / 1: line kernel, 2: register-plane kernel, 3: even-odd line kernel
   int fp64_variant = 0;   // 0: even-odd line kernel, 1: plain line kernel
 };
@@ -139,6 +141,9 @@ cudaError_t apply_cc_f64(const fe_ctx* c, const double* X, double* Y, int n_vec,
 cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);
 cudaError_t diagonal_f64(const fe_ctx* c, double* diag, cudaStream_t s);
 cudaError_t apply_mma_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s, fe_mode mode);
+cudaError_t apply_df64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s);
+cudaError_t apply_scaled_df64(const fe_ctx* c, const double* X, double* Y, int n_vec, const Scale<double>& sc,
+                              cudaStream_t s);
 cudaError_t apply_scaled_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, const Scale<double>& sc,
                              cudaStream_t s);
 cudaError_t apply_scaled_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, const Scale<float>& sc,

@@ -49,7 +49,7 @@ extern "C" fe_status fe_apply_host_noalloc(fe_ctx* c, const void* Xh, void* Yh, 
   if (!c || n_vec < 0) return FE_EINVAL;
   if (n_vec == 0) return FE_OK;
   if (!Xh || !Yh) return FE_EINVAL;
-  const size_t elem = c->mode == FE_FP64 ? sizeof(double) : sizeof(float);
+  const size_t elem = (c->mode == FE_FP64 || c->mode == FE_DF64) ? sizeof(double) : sizeof(float);
   const size_t bytes = c->n_dofs * (size_t)n_vec * elem;
   // X and Y both live in the array, Y at the next 256-byte boundary after X
   const size_t y_off = (bytes + 255) / 256 * 256;

@@ -159,16 +159,25 @@ cudaError_t upload_as_float(float** dst, const std::vector<T>& src) {
   return upload(dst, f.data(), f.size());
 }
 
+cudaError_t upload_as_ff(ff** dst, const std::vector<double>& src) {
+  std::vector<ff> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = ff(src[i]);
+  return upload(dst, tmp.data(), tmp.size());
+}
+
 }  // namespace
 
-// Geometry and per-point value coefficient uploads (FP64 and FP32 copies).
+// Geometry and per-point value coefficient uploads (FP64, FP32 and double-float copies).
 cudaError_t upload_point_coeff(fe_ctx* c, const std::vector<double>& ptC) {
   cudaFree(c->d_ptC64);
   cudaFree(c->d_ptC32);
+  cudaFree(c->d_ptCff);
   c->d_ptC64 = nullptr;
   c->d_ptC32 = nullptr;
+  c->d_ptCff = nullptr;
   cudaError_t e = upload(&c->d_ptC64, ptC.data(), ptC.size());
   if (e == cudaSuccess) e = upload_as_float(&c->d_ptC32, ptC);
+  if (e == cudaSuccess) e = upload_as_ff(&c->d_ptCff, ptC);
   return e;
 }
 
@@ -247,8 +256,9 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
   // FP64 tile measured on GB300: 8 vectors x 16 lines up to n_q = 8, 4 x 32 above;
   // FP32: even-odd line kernel, 8 x 32 up to n_q = 8, 4 x 64 above (two more
   // CTAs per SM in the 48 KB of shared memory that 4 vectors of n_q = 10 take)
+  // double-float: 8 x 32 up to n_q = 8, 4 x 64 above
   c->fp32_variant = 3;
-  if (quad->n_q >= 9) { c->vb64 = 4; c->nty64 = 32; c->vb32 = 4; c->nty32 = 64; }
+  if (quad->n_q >= 9) { c->vb64 = 4; c->nty64 = 32; c->vb32 = 4; c->nty32 = 64; c->vbdf = 4; c->ntydf = 64; }
   const int np = c->np, nq = c->nq;
   const int add = c->periodic ? 0 : 1;
   c->mdev.nx = c->nx; c->mdev.ny = c->ny; c->mdev.nz = c->nz;
@@ -346,6 +356,8 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
   if (err == cudaSuccess && !c->general) err = upload_as_float(&c->d_cellG32, c->cellG);
   if (err == cudaSuccess && c->general) err = upload(&c->d_ptG64, c->ptG.data(), c->ptG.size());
   if (err == cudaSuccess && c->general) err = upload_as_float(&c->d_ptG32, c->ptG);
+  if (err == cudaSuccess && !c->general) err = upload_as_ff(&c->d_cellGff, c->cellG);
+  if (err == cudaSuccess && c->general) err = upload_as_ff(&c->d_ptGff, c->ptG);
   if (err == cudaSuccess) err = cudaMalloc(&c->d_status, sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(c->d_status, 0, sizeof(int));
   if (err == cudaSuccess) {
@@ -361,6 +373,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
   if (!c) return;
   cudaFree(c->d_cells); cudaFree(c->d_cellG64); cudaFree(c->d_ptG64); cudaFree(c->d_ptC64);
   cudaFree(c->d_cellG32); cudaFree(c->d_ptG32); cudaFree(c->d_ptC32); cudaFree(c->d_detJ);
+  cudaFree(c->d_cellGff); cudaFree(c->d_ptGff); cudaFree(c->d_ptCff);
   cudaFree(c->d_status); cudaFree(c->d_stage);
   if (c->copy_in) cudaStreamDestroy(c->copy_in);
   if (c->copy_out) cudaStreamDestroy(c->copy_out);
@@ -422,7 +435,7 @@ extern "C" fe_status fe_set_potential(fe_ctx* c, const double* Vq) {
 
 extern "C" fe_status fe_set_mode(fe_ctx* c, fe_mode m) {
   if (!c) return FE_EINVAL;
-  if (m != FE_FP64 && m != FE_FP32 && m != FE_TF32 && m != FE_BF16 && m != FE_TF32X3) return FE_EINVAL;
+  if (m != FE_FP64 && m != FE_FP32 && m != FE_TF32 && m != FE_BF16 && m != FE_TF32X3 && m != FE_DF64) return FE_EINVAL;
   c->mode = m;
   return FE_OK;
 }
@@ -438,6 +451,10 @@ extern "C" fe_status fe_set_tile(fe_ctx* c, fe_mode mode, int vectors_per_cta, i
     c->vb64 = vectors_per_cta;
     c->nty64 = lines;
     c->fp64_variant = variant;
+  } else if (mode == FE_DF64) {
+    if (variant != 0) return FE_EINVAL;
+    c->vbdf = vectors_per_cta;
+    c->ntydf = lines;
   } else if (mode == FE_FP32) {
     if (variant == 2 && c->nq > 8) return FE_EUNSUPPORTED;
     c->vb32 = vectors_per_cta;

@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libfe.so")
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOTCONV, FE_EBREAKDOWN, FE_ENONFINITE, FE_ETIMEOUT, FE_EUNSUPPORTED = range(9)
 FE_BC_DIRICHLET0, FE_BC_PERIODIC = 0, 1
 FE_QUAD_GAUSS, FE_QUAD_GLL = 0, 1
-FE_FP64, FE_FP32, FE_TF32, FE_BF16, FE_TF32X3 = 0, 1, 2, 3, 4
-MODES = {"fp64": FE_FP64, "fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16, "tf32x3": FE_TF32X3}
+FE_FP64, FE_FP32, FE_TF32, FE_BF16, FE_TF32X3, FE_DF64 = 0, 1, 2, 3, 4, 5
+MODES = {"fp64": FE_FP64, "fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16, "tf32x3": FE_TF32X3, "df64": FE_DF64}
 
 
 class FeError(RuntimeError):
@@ -244,7 +244,7 @@ def fe_get_mode(ctx: int) -> int:
 def _check_block(ctx: int, t, what: str):
     import torch
     mode = fe_get_mode(ctx)
-    want = torch.float64 if mode == FE_FP64 else torch.float32
+    want = torch.float64 if mode in (FE_FP64, FE_DF64) else torch.float32
     if not t.is_cuda or t.dtype != want or not t.is_contiguous() or t.dim() != 2 or t.shape[0] != fe_num_dofs(ctx):
         raise ValueError(f"{what}: need a contiguous CUDA {want} tensor of shape (num_dofs, n_vec)")
 

@@ -23,7 +23,8 @@ FP64_TOL = 1e-12
 FP32_TOL = 2e-6
 # split TF32 (hi + lo operands, three products, only lo*lo dropped) is held to
 # the FP32 bound: the dropped term is 2^-22 relative per product.
-TOL = {"fp64": FP64_TOL, "fp32": FP32_TOL, "tf32": 5e-3, "bf16": 5e-2, "tf32x3": FP32_TOL}
+# double-float arithmetic (FP64 data, pairs of FP32 in the kernel) is held to the FP64 bound.
+TOL = {"fp64": FP64_TOL, "fp32": FP32_TOL, "tf32": 5e-3, "bf16": 5e-2, "tf32x3": FP32_TOL, "df64": FP64_TOL}
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +56,7 @@ def _setup_pair(fe, nx, ny, nz, p, nq, periodic=False, vertices=None, quad=0, po
 
 def _gpu_apply(fe, ctx, X, mode):
     fe.fe_set_mode(ctx, mode)
-    dt = torch.float64 if mode == "fp64" else torch.float32
+    dt = torch.float64 if mode in ("fp64", "df64") else torch.float32
     Xd = torch.from_numpy(X).to(device="cuda", dtype=dt).contiguous()
     Yd = torch.full_like(Xd, float("nan"))
     fe.fe_apply(ctx, Xd, Yd)
@@ -85,7 +86,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32", "bf16", "tf32x3"])
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32", "bf16", "tf32x3", "df64"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}_p{c[3]}_q{c[4]}"
                          f"_{'per' if c[5] else 'dir'}{'_dist' if c[6] else ''}_nv{c[8]}")
 def test_apply_matches_oracle(fe, case, mode):
@@ -158,7 +159,7 @@ def test_host_buffer_apply(fe):
         fe.fe_destroy(ctx)
 
 
-@pytest.mark.parametrize("mode,n_vec", [("fp64", 37), ("fp32", 70), ("tf32", 64), ("tf32x3", 33)])
+@pytest.mark.parametrize("mode,n_vec", [("fp64", 37), ("fp32", 70), ("tf32", 64), ("tf32x3", 33), ("df64", 40)])
 def test_host_buffer_apply_pipelined(fe, mode, n_vec):
     """Blocks of at least two 128-byte chunks go through the copy/compute
     pipeline (ragged last chunk here); every column must equal the device
@@ -166,7 +167,7 @@ def test_host_buffer_apply_pipelined(fe, mode, n_vec):
     ctx, mesh, Vo = _setup_pair(fe, 3, 2, 3, 4, 6)
     try:
         fe.fe_set_mode(ctx, mode)
-        dt = torch.float64 if mode == "fp64" else torch.float32
+        dt = torch.float64 if mode in ("fp64", "df64") else torch.float32
         X = torch.from_numpy(inputs.random_block(fe.fe_num_dofs(ctx), n_vec, "uniform", 5)).to(dt)
         Xh = X.pin_memory()
         Yh = torch.full_like(Xh, float("nan")).pin_memory()
@@ -208,7 +209,7 @@ def _sample_rows(n, mesh, p, count, seed):
 
 @pytest.mark.parametrize("name,mode", [("c1", "fp64"), ("c2", "fp64"), ("c2", "fp32"), ("c3", "fp64"),
                                        ("c3", "fp32"), ("c3", "tf32"), ("c3", "bf16"), ("c3", "tf32x3"),
-                                       ("c2", "tf32"), ("c2", "tf32x3"),
+                                       ("c2", "tf32"), ("c2", "tf32x3"), ("c2", "df64"), ("c3", "df64"),
                                        ("c5", "fp64")])
 def test_full_size_sampled_rows(fe, name, mode):
     """Full-size workloads in the benchmark's launch configuration, checked on
