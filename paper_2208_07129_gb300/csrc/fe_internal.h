@@ -120,6 +120,7 @@ struct fe_ctx {
   cudaEvent_t ev_start = nullptr, ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
   fe_mode mode = FE_FP64;
   fe_mode inner_mode = FE_FP32;   // arithmetic of the inner solve (refinement)
+  fe_mode op64 = FE_FP64;         // operator of FP64-data PCG: FE_FP64, or FE_DF64 (double-float)
   fe::SolveWs ws;
   fe::LearnedPrecond* learned = nullptr;
   // eigenvalue layer: GLL diagonal mass (host), M^-1/2 on the device, and the

@@ -208,7 +208,7 @@ cudaError_t solver_workspace(fe_ctx* c, int nv) {
 template <typename T>
 static fe_status apply_mode(fe_ctx* c, const T* X, T* Y, int nv, cudaStream_t s) {
   const fe_mode saved = c->mode;
-  c->mode = sizeof(T) == 8 ? FE_FP64 : c->inner_mode;
+  c->mode = sizeof(T) == 8 ? c->op64 : c->inner_mode;
   fe_status st = fe_apply(c, X, Y, nv, s);
   c->mode = saved;
   return st;
@@ -374,7 +374,7 @@ extern "C" fe_status fe_solve(fe_ctx* c, const double* B, double* X, int nv, dou
   if (!c || !B || !X || nv <= 0 || !(rtol > 0.0) || max_it < 0) return FE_EINVAL;
   if (precond != FE_PRECOND_NONE && precond != FE_PRECOND_JACOBI && precond != FE_PRECOND_LEARNED) return FE_EINVAL;
   if (inner_mode != FE_FP64 && inner_mode != FE_FP32 && inner_mode != FE_TF32 && inner_mode != FE_BF16 &&
-      inner_mode != FE_TF32X3)
+      inner_mode != FE_TF32X3 && inner_mode != FE_DF64)
     return FE_EINVAL;
   if (precond == FE_PRECOND_LEARNED && !learned_ready(c, nv)) return FE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -399,14 +399,17 @@ extern "C" fe_status fe_solve(fe_ctx* c, const double* B, double* X, int nv, dou
   fe_solve_info inf{};
   fe_status st = FE_OK;
   int fp64_applies = 0;
-  if (inner_mode == FE_FP64) {
-    // plain FP64 PCG; the recurrence residual is trusted to rtol/2, then the
-    // FP64 operator judges.
+  if (inner_mode == FE_FP64 || inner_mode == FE_DF64) {
+    // FP64 PCG (operator in FP64, or in double-float arithmetic for
+    // FE_DF64); the recurrence residual is trusted to rtol/2, then the FP64
+    // operator judges.
     for (int j = 0; j < nv; ++j) tol[j] = 0.5 * rtol * bnorm[j];
     int its = 0;
+    c->op64 = (fe_mode)inner_mode;
     st = pcg<double>(c, B, X, nv, tol.data(), max_it, precond, s, w.v64[0], w.v64[1], w.v64[2], w.v64[3], &its, 1);
+    c->op64 = FE_FP64;
     inf.iterations = its;
-    fp64_applies = its + 1;
+    fp64_applies = inner_mode == FE_FP64 ? its + 1 : 1;
   } else {
     // FP64 iterative refinement: r = b - A64 x; solve A32 d = r / ||r|| in the
     // inner precision to the reduction still needed (rtol ||b|| / ||r||), but

@@ -39,7 +39,8 @@ def _problem(fe, nx=3, p=4, nq=6, n_vec=6, distorted=False, seed=0):
 
 
 @pytest.mark.parametrize("precond,inner", [("jacobi", "fp64"), ("none", "fp64"), ("jacobi", "fp32"),
-                                           ("jacobi", "tf32"), ("jacobi", "bf16"), ("jacobi", "tf32x3")])
+                                           ("jacobi", "tf32"), ("jacobi", "bf16"), ("jacobi", "tf32x3"),
+                                           ("jacobi", "df64")])
 def test_pcg_solution(fe, precond, inner):
     ctx, B, Xref = _problem(fe, distorted=(inner != "fp64"))
     try:
@@ -53,7 +54,10 @@ def test_pcg_solution(fe, precond, inner):
         X = Xd.cpu().numpy()
         err = np.linalg.norm(X - Xref) / np.linalg.norm(Xref)
         assert err < 1e-6, err
-        if inner != "fp64":
+        if inner == "df64":
+            # FP64 PCG on the double-float operator: only the judge is an FP64 apply
+            assert res["outer_iterations"] == 0 and res["fp64_applies"] == 1
+        elif inner != "fp64":
             # FP64 refinement around the reduced-precision inner solve: one FP64
             # residual per outer step, plus the initial and the judging one
             assert res["outer_iterations"] >= 1 and res["fp64_applies"] == res["outer_iterations"] + 2
