@@ -409,7 +409,7 @@ extern "C" fe_status fe_solve(fe_ctx* c, const double* B, double* X, int nv, dou
     st = pcg<double>(c, B, X, nv, tol.data(), max_it, precond, s, w.v64[0], w.v64[1], w.v64[2], w.v64[3], &its, 1);
     c->op64 = FE_FP64;
     inf.iterations = its;
-    fp64_applies = inner_mode == FE_FP64 ? its + 1 : 1;
+    fp64_applies = inner_mode == FE_FP64 ? its + 1 : 0;   // the judge below adds one
   } else {
     // FP64 iterative refinement: r = b - A64 x; solve A32 d = r / ||r|| in the
     // inner precision to the reduction still needed (rtol ||b|| / ||r||), but
