@@ -98,6 +98,44 @@ typedef struct {
  * handle owned by the caller (free with fe_destroy).  Synchronous. */
 fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_desc* quad, double mu, fe_ctx** out);
 
+/* One-level adaptively refined mesh with hanging nodes (Sec. 3.2.2; the
+ * adaptive meshes of the paper's Sec. 4 benchmarks).  A Dirichlet box
+ * [lo, hi] of nx x ny x nz coarse cells of size H per direction; the coarse
+ * cells with index in [refine_lo, refine_hi) per direction are split once
+ * into 2 x 2 x 2 children of size H / 2.
+ *  - Cells: coarse cell by coarse cell (x fastest), a refined cell replaced by
+ *    its 8 children (x fastest); V at quadrature points follows this order
+ *    (fe_quadrature_points, fe_set_potential).
+ *  - Nodes: the (p+1)^3 GLL nodes of every cell.  Along one direction a node
+ *    sits at a vertex m H/2 of the half-size grid, at an interior GLL node of
+ *    a coarse cell c (c H + (1 + g_i) H/2; the middle node of an even degree
+ *    is the vertex 2c + 1) or at an interior GLL node of a fine cell f
+ *    (f H/2 + (1 + g_j) H/4); nodes of different cells at the same point are
+ *    one DoF.  DoFs are numbered by position, z slowest and x fastest.
+ *  - Hanging nodes: a node of a fine cell on the closure of an unrefined
+ *    coarse cell C that is not one of C's nodes is a slave, u_s =
+ *    sum_m phi_m^C(x_s) u_m over C's nodes (C's interpolant; masters on the
+ *    boundary carry 0).  The product is Y = C^T A C X on the free rows (C:
+ *    free values -> all nodes) with the slave and Dirichlet rows of Y written
+ *    0 and those entries of X ignored.
+ * Supported on such a context: fe_num_*, fe_quadrature_points,
+ * fe_set_potential, fe_set_mode (FE_FP64, FE_DF64, FE_FP32), fe_set_tile,
+ * fe_apply, fe_apply_host, fe_destroy; the other calls return
+ * FE_EUNSUPPORTED.  Synchronous. */
+typedef struct {
+  int nx, ny, nz;
+  double lo[3], hi[3];
+  int refine_lo[3], refine_hi[3];
+} fe_refined_desc;
+fe_status fe_setup_refined(const fe_refined_desc* mesh, int p, const fe_quad_desc* quad, double mu, fe_ctx** out);
+
+/* Number of hanging (slave) nodes of a refined-mesh context (0 otherwise). */
+int fe_num_slaves(const fe_ctx* ctx);
+
+/* Physical coordinates of every DoF: xyz_host[dof * 3 + d] (host, FP64,
+ * num_dofs x 3), for evaluating data at the nodes.  Synchronous. */
+fe_status fe_node_coords(const fe_ctx* ctx, double* xyz_host);
+
 /* Release everything the context owns.  NULL is allowed. */
 void fe_destroy(fe_ctx* ctx);
 

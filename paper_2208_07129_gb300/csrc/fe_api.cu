@@ -26,6 +26,10 @@ extern "C" fe_status fe_apply(fe_ctx* c, const void* X, void* Y, int n_vec, void
   if (overlaps(X, Y, bytes)) return FE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
+  if (c->refined) {
+    if (c->mode != FE_FP64 && c->mode != FE_DF64 && c->mode != FE_FP32) return FE_EUNSUPPORTED;
+    return from_cuda(apply_refined(c, X, Y, n_vec, s));
+  }
   switch (c->mode) {
     case FE_FP64: e = apply_cc_f64(c, static_cast<const double*>(X), static_cast<double*>(Y), n_vec, s); break;
     case FE_DF64: e = apply_df64(c, static_cast<const double*>(X), static_cast<double*>(Y), n_vec, s); break;
@@ -146,6 +150,7 @@ extern "C" fe_status fe_apply_host(fe_ctx* c, const void* Xh, void* Yh, int n_ve
 
 extern "C" fe_status fe_diagonal(fe_ctx* c, double* diag, void* stream) {
   if (!c || !diag) return FE_EINVAL;
+  if (c->refined) return FE_EUNSUPPORTED;
   return from_cuda(diagonal_f64(c, diag, static_cast<cudaStream_t>(stream)));
 }
 

@@ -334,7 +334,8 @@ extern "C" fe_status fe_batch_create(fe_ctx* const* ctxs, int n, const int* n_ve
   if (mode != FE_FP64 && mode != FE_FP32) return FE_EUNSUPPORTED;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || n_vec[i] <= 0) return FE_EINVAL;
-    if (ctxs[i]->general || ctxs[i]->p < 3 || ctxs[i]->p > 8 || ctxs[i]->nq != ctxs[i]->p + 2) return FE_EUNSUPPORTED;
+    if (ctxs[i]->general || ctxs[i]->refined || ctxs[i]->p < 3 || ctxs[i]->p > 8 || ctxs[i]->nq != ctxs[i]->p + 2)
+      return FE_EUNSUPPORTED;
   }
   fe_batch* b = new fe_batch();
   b->n = n;

@@ -475,6 +475,7 @@ void free_eig(fe_ctx* c) {
 
 extern "C" fe_status fe_mass_gll(fe_ctx* c, double* m_host) {
   if (!c || !m_host) return FE_EINVAL;
+  if (c->refined) return FE_EUNSUPPORTED;
   build_gll_mass(c);
   std::copy(c->mass.begin(), c->mass.end(), m_host);
   return FE_OK;
@@ -485,7 +486,7 @@ extern "C" fe_status fe_apply_scaled(fe_ctx* c, const void* X, void* Y, int n_ve
   if (!c || n_vec < 0) return FE_EINVAL;
   if (n_vec == 0) return FE_OK;
   if (!X || !Y || !std::isfinite(a) || !std::isfinite(b) || !std::isfinite(cc)) return FE_EINVAL;
-  if (c->mode != FE_FP64 && c->mode != FE_FP32 && c->mode != FE_DF64) return FE_EUNSUPPORTED;
+  if (c->refined || (c->mode != FE_FP64 && c->mode != FE_FP32 && c->mode != FE_DF64)) return FE_EUNSUPPORTED;
   const int prec = c->mode == FE_FP64 ? kF64 : (c->mode == FE_DF64 ? kDF64 : kF32);
   if (overlaps(X, Y, c->n_dofs * (size_t)n_vec * (prec != kF32 ? 8 : 4))) return FE_EINVAL;
   cudaError_t e = ensure_msq(c);
@@ -498,7 +499,7 @@ extern "C" fe_status fe_chebyshev_filter(fe_ctx* c, void* X, void* Y, int n_vec,
   if (!c || n_vec < 0 || degree < 1) return FE_EINVAL;
   if (n_vec == 0) return FE_OK;
   if (!X || !Y || !(lmin < lu && lu < lmax) || !std::isfinite(lmin) || !std::isfinite(lmax)) return FE_EINVAL;
-  if (c->mode != FE_FP64 && c->mode != FE_FP32 && c->mode != FE_DF64) return FE_EUNSUPPORTED;
+  if (c->refined || (c->mode != FE_FP64 && c->mode != FE_FP32 && c->mode != FE_DF64)) return FE_EUNSUPPORTED;
   const int prec = c->mode == FE_FP64 ? kF64 : (c->mode == FE_DF64 ? kDF64 : kF32);
   const size_t bytes = c->n_dofs * (size_t)n_vec * (prec != kF32 ? 8 : 4);
   if (overlaps(X, Y, bytes)) return FE_EINVAL;
@@ -518,6 +519,7 @@ extern "C" fe_status fe_chfsi(fe_ctx* c, double* U, int k, const fe_chfsi_desc* 
   if (k < 2 || d->n_wanted < 1 || d->n_wanted > k || d->degree < 1 || d->max_iter < 1 || d->lanczos_steps < 2 ||
       !(d->tol > 0) || (d->filter_mode != FE_FP64 && d->filter_mode != FE_FP32 && d->filter_mode != FE_DF64))
     return FE_EINVAL;
+  if (c->refined) return FE_EUNSUPPORTED;
   size_t free_dofs = c->n_dofs;
   if (!c->periodic) free_dofs = (size_t)(c->mdev.Nx - 2) * (c->mdev.Ny - 2) * (c->mdev.Nz - 2);
   if ((size_t)k > free_dofs) return FE_EINVAL;

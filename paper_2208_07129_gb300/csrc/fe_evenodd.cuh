@@ -60,12 +60,14 @@ __device__ __forceinline__ void eo_apply(const EOTab<T, NO, NI>& t, const T* in,
 }
 
 // Same as cell_body (identical data flow, tiles and assembly, the same SC
-// epilogue), with every 1D contraction in even-odd form.
-template <typename T, int NP, int NQ, bool GEN, bool SC = false>
+// epilogue), with every 1D contraction in even-odd form.  With MAP the cell's
+// nodes come from an explicit map (see map_node) instead of the structured
+// numbering: the refined meshes with hanging nodes.
+template <typename T, int NP, int NQ, bool GEN, bool SC = false, bool MAP = false>
 __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, const MeshDev& m, const Geom<T>& geo,
                                              int e, int vb, int B, int v, int ty, int nty, int n_vec,
                                              const T* __restrict__ X, T* __restrict__ Y, T* smem,
-                                             const Scale<T>& sc = Scale<T>{}) {
+                                             const Scale<T>& sc = Scale<T>{}, const int* __restrict__ map = nullptr) {
   constexpr int P = NP - 1;
   constexpr int NQ3 = NQ * NQ * NQ;
   T* ST = smem;
@@ -84,10 +86,19 @@ __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, con
     T u[NP], a[NQ];
 #pragma unroll
     for (int i1 = 0; i1 < NP; ++i1) {
-      const int gx = node_coord(cx, i1, P, m.Nx, m.periodic);
-      const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
-      u[i1] = (active && !con) ? __ldg(X + (row + gx) * n_vec + vg) : T(0);
-      if constexpr (SC) u[i1] *= __ldg(sc.msq + row + gx);
+      size_t node;
+      bool con;
+      if constexpr (MAP) {
+        const int code = __ldg(map + (size_t)e * NP * NP * NP + l * NP + i1);
+        node = (size_t)(code & kMapIndex);
+        con = (code & kMapConstrained) != 0;
+      } else {
+        const int gx = node_coord(cx, i1, P, m.Nx, m.periodic);
+        node = row + gx;
+        con = con_yz || on_boundary(gx, m.Nx, m.periodic);
+      }
+      u[i1] = (active && !con) ? __ldg(X + node * n_vec + vg) : T(0);
+      if constexpr (SC) u[i1] *= __ldg(sc.msq + node);
     }
     eo_apply<T, NQ, NP, 1>(tab.N, u, a);
 #pragma unroll
@@ -219,12 +230,22 @@ __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, con
     const size_t row = (size_t)(gy + (size_t)m.Ny * gz) * m.Nx;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      const int gx = node_coord(cx, i, P, m.Nx, m.periodic);
-      const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
-      const bool first = first_yz && first_along(cx, m.nx, i, P, m.periodic, m.last_odd_x);
-      T* dst = Y + (row + gx) * n_vec + vg;
+      size_t node;
+      bool con, first;
+      if constexpr (MAP) {
+        const int code = __ldg(map + (size_t)e * NP * NP * NP + l * NP + i);
+        node = (size_t)(code & kMapIndex);
+        con = (code & kMapConstrained) != 0;
+        first = (code & kMapFirst) != 0;
+      } else {
+        const int gx = node_coord(cx, i, P, m.Nx, m.periodic);
+        node = row + gx;
+        con = con_yz || on_boundary(gx, m.Nx, m.periodic);
+        first = first_yz && first_along(cx, m.nx, i, P, m.periodic, m.last_odd_x);
+      }
+      T* dst = Y + node * n_vec + vg;
       if constexpr (SC) {
-        scaled_store(dst, X + (row + gx) * n_vec + vg, sc.a * __ldg(sc.msq + row + gx) * o[i], first, con, sc);
+        scaled_store(dst, X + node * n_vec + vg, sc.a * __ldg(sc.msq + node) * o[i], first, con, sc);
       } else {
         if (first) *dst = con ? T(0) : o[i];
         else if (!con) *dst += o[i];

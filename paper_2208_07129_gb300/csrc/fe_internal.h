@@ -13,6 +13,11 @@ namespace fe {
 constexpr int kMaxP = 8;
 constexpr int kMaxNQ = kMaxP + 3;
 
+// Entries of the explicit cell -> DoF map of refined meshes: the DoF index in
+// the low 29 bits, bit 29 set for a Dirichlet node, bit 30 set when this
+// (cell, node) is the node's first writer in colour order.
+constexpr int kMapIndex = (1 << 29) - 1, kMapConstrained = 1 << 29, kMapFirst = 1 << 30;
+
 // Structured-mesh description as the kernels see it.
 struct MeshDev {
   int nx, ny, nz;     // cells
@@ -121,6 +126,24 @@ struct fe_ctx {
   fe_mode mode = FE_FP64;
   fe_mode inner_mode = FE_FP32;   // arithmetic of the inner solve (refinement)
   fe_mode op64 = FE_FP64;         // operator of FP64-data PCG: FE_FP64, or FE_DF64 (double-float)
+  // one-level refined mesh with hanging nodes: explicit cell -> DoF map and
+  // the constraints u_S = W u_M (slave rows for the distribute step, master
+  // rows for the condense step)
+  int refined = 0;
+  int* d_map = nullptr;                 // E x n_p^3 entries (kMap* bits)
+  std::vector<double> cell_lo, cell_h;  // per cell: box corner and size (3 each)
+  std::vector<double> node_xyz;         // per DoF: physical coordinates
+  int n_slaves = 0, n_masters = 0;
+  int* d_row_slave = nullptr;           // per DoF: its slave number, or -1
+  int *d_sl_ptr = nullptr, *d_sl_idx = nullptr;   // slave -> masters (CSR)
+  double* d_sl_w = nullptr;
+  float* d_sl_w32 = nullptr;
+  int *d_slaves = nullptr;              // DoF of each slave
+  int *d_ma_rows = nullptr, *d_ma_ptr = nullptr, *d_ma_idx = nullptr;   // master -> slaves (CSR)
+  double* d_ma_w = nullptr;
+  float* d_ma_w32 = nullptr;
+  void* d_xc = nullptr;                 // X with the slave rows filled in
+  size_t xc_bytes = 0;
   fe::SolveWs ws;
   fe::LearnedPrecond* learned = nullptr;
   // eigenvalue layer: GLL diagonal mass (host), M^-1/2 on the device, and the
@@ -149,6 +172,17 @@ cudaError_t apply_scaled_f64(const fe_ctx* c, const double* X, double* Y, int n_
                              cudaStream_t s);
 cudaError_t apply_scaled_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, const Scale<float>& sc,
                              cudaStream_t s);
+// Setup helpers shared by the structured and the refined-mesh setup (fe_setup.cu).
+void build_tables(fe_ctx* c);
+double lagrange_1d(const double* xs, int n, int k, double t);
+cudaError_t upload_point_coeff(fe_ctx* c, const std::vector<double>& ptC);
+cudaError_t upload_ints(int** dst, const std::vector<int>& src);
+cudaError_t upload_doubles(double** dst, const std::vector<double>& src);
+cudaError_t upload_floats(float** dst, const std::vector<double>& src);
+cudaError_t upload_ffs(ff** dst, const std::vector<double>& src);
+// Refined meshes with hanging nodes (fe_refined.cu / fe_apply_refined.cu).
+cudaError_t apply_refined(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s);
+void free_refined(fe_ctx* c);
 // GLL diagonal mass of Sec. 4.3 into c->mass (host, FP64; constrained rows 1).
 void build_gll_mass(fe_ctx* c);
 void free_eig(fe_ctx* c);

@@ -890,6 +890,7 @@ using namespace fe;
 
 extern "C" fe_status fe_precond_init(fe_ctx* c, unsigned long long seed) {
   if (!c) return FE_EINVAL;
+  if (c->refined) return FE_EUNSUPPORTED;
   cudaError_t e = alloc_learned(c);
   if (e != cudaSuccess) return from_cuda(e);
   LearnedPrecond* L = c->learned;

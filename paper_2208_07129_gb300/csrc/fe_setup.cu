@@ -167,6 +167,35 @@ cudaError_t upload_as_ff(ff** dst, const std::vector<double>& src) {
 
 }  // namespace
 
+// GLL nodes and weights (n_p points), the quadrature rule, and the 1D
+// tables: N (values at the points) and D~ (collocation derivative), plain
+// and with sqrt(w) folded in (Sec. 3.2.4).  Needs c->np, c->nq, c->quad_kind.
+void build_tables(fe_ctx* c) {
+  const int np = c->np, nq = c->nq;
+  c->gll.resize(np); c->wgll.resize(np); c->qx.resize(nq); c->qw.resize(nq);
+  gll_rule(np, c->gll.data(), c->wgll.data());
+  if (c->quad_kind == FE_QUAD_GAUSS) gauss_rule(nq, c->qx.data(), c->qw.data());
+  else gll_rule(nq, c->qx.data(), c->qw.data());
+  c->N1.resize(nq * np); c->D1.resize(nq * nq); c->Nf.resize(nq * np); c->Df.resize(nq * nq);
+  for (int q = 0; q < nq; ++q) {
+    for (int i = 0; i < np; ++i) {
+      c->N1[q * np + i] = lagrange_value(c->gll.data(), np, i, c->qx[q]);
+      c->Nf[q * np + i] = c->N1[q * np + i] * std::sqrt(c->qw[q]);
+    }
+    for (int k = 0; k < nq; ++k) {
+      c->D1[q * nq + k] = lagrange_deriv(c->qx.data(), nq, k, c->qx[q]);
+      c->Df[q * nq + k] = c->D1[q * nq + k] * std::sqrt(c->qw[q] / c->qw[k]);
+    }
+  }
+}
+
+double lagrange_1d(const double* xs, int n, int k, double t) { return lagrange_value(xs, n, k, t); }
+
+cudaError_t upload_ints(int** dst, const std::vector<int>& src) { return upload(dst, src.data(), src.size()); }
+cudaError_t upload_doubles(double** dst, const std::vector<double>& src) { return upload(dst, src.data(), src.size()); }
+cudaError_t upload_floats(float** dst, const std::vector<double>& src) { return upload_as_float(dst, src); }
+cudaError_t upload_ffs(ff** dst, const std::vector<double>& src) { return upload_as_ff(dst, src); }
+
 // Geometry and per-point value coefficient uploads (FP64, FP32 and double-float copies).
 cudaError_t upload_point_coeff(fe_ctx* c, const std::vector<double>& ptC) {
   cudaFree(c->d_ptC64);
@@ -276,21 +305,7 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
   }
 
   // ---- 1D tables ----
-  c->gll.resize(np); c->wgll.resize(np); c->qx.resize(nq); c->qw.resize(nq);
-  gll_rule(np, c->gll.data(), c->wgll.data());
-  if (quad->kind == FE_QUAD_GAUSS) gauss_rule(nq, c->qx.data(), c->qw.data());
-  else gll_rule(nq, c->qx.data(), c->qw.data());
-  c->N1.resize(nq * np); c->D1.resize(nq * nq); c->Nf.resize(nq * np); c->Df.resize(nq * nq);
-  for (int q = 0; q < nq; ++q) {
-    for (int i = 0; i < np; ++i) {
-      c->N1[q * np + i] = lagrange_value(c->gll.data(), np, i, c->qx[q]);
-      c->Nf[q * np + i] = c->N1[q * np + i] * std::sqrt(c->qw[q]);
-    }
-    for (int k = 0; k < nq; ++k) {
-      c->D1[q * nq + k] = lagrange_deriv(c->qx.data(), nq, k, c->qx[q]);
-      c->Df[q * nq + k] = c->D1[q * nq + k] * std::sqrt(c->qw[q] / c->qw[k]);
-    }
-  }
+  build_tables(c);
 
   // ---- geometry (FP64) ----
   const size_t E = c->n_cells, nq3 = (size_t)nq * nq * nq;
@@ -382,6 +397,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
   free_solver_workspace(c);
   free_learned(c);
   free_eig(c);
+  free_refined(c);
   delete c;
 }
 
@@ -393,6 +409,18 @@ extern "C" fe_status fe_quadrature_points(const fe_ctx* c, double* xyz) {
   if (!c || !xyz) return FE_EINVAL;
   const int nq = c->nq;
   const size_t nq3 = (size_t)nq * nq * nq;
+  if (c->refined) {   // axis-aligned boxes of the refined mesh, in cell order
+    for (size_t e = 0; e < c->n_cells; ++e)
+      for (int q3 = 0; q3 < nq; ++q3)
+        for (int q2 = 0; q2 < nq; ++q2)
+          for (int q1 = 0; q1 < nq; ++q1) {
+            const size_t Q = q1 + (size_t)nq * (q2 + (size_t)nq * q3);
+            const int qq[3] = {q1, q2, q3};
+            for (int d = 0; d < 3; ++d)
+              xyz[(e * nq3 + Q) * 3 + d] = c->cell_lo[3 * e + d] + 0.5 * (1.0 + c->qx[qq[d]]) * c->cell_h[3 * e + d];
+          }
+    return FE_OK;
+  }
   fe_mesh_desc md{};
   md.nx = c->nx; md.ny = c->ny; md.nz = c->nz;
   for (int cz = 0; cz < c->nz; ++cz)

@@ -372,6 +372,7 @@ void free_solver_workspace(fe_ctx* c) {
 extern "C" fe_status fe_solve(fe_ctx* c, const double* B, double* X, int nv, double rtol, int max_it, int precond,
                               int inner_mode, fe_solve_info* info, double* rel_res, void* stream) {
   if (!c || !B || !X || nv <= 0 || !(rtol > 0.0) || max_it < 0) return FE_EINVAL;
+  if (c->refined) return FE_EUNSUPPORTED;
   if (precond != FE_PRECOND_NONE && precond != FE_PRECOND_JACOBI && precond != FE_PRECOND_LEARNED) return FE_EINVAL;
   if (inner_mode != FE_FP64 && inner_mode != FE_FP32 && inner_mode != FE_TF32 && inner_mode != FE_BF16 &&
       inner_mode != FE_TF32X3 && inner_mode != FE_DF64)

@@ -85,6 +85,12 @@ class fe_chfsi_info(ctypes.Structure):
                 ("seconds_rr", ctypes.c_double)]
 
 
+class fe_refined_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("refine_lo", ctypes.c_int * 3), ("refine_hi", ctypes.c_int * 3)]
+
+
 class fe_quad_desc(ctypes.Structure):
     _fields_ = [("n_q", ctypes.c_int), ("kind", ctypes.c_int)]
 
@@ -138,6 +144,10 @@ def lib() -> ctypes.CDLL:
         "fe_precond_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
         "fe_mlp_gradients": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
         "fe_mass_gll": (ctypes.c_int, [_VP, _DP]),
+        "fe_setup_refined": (ctypes.c_int, [ctypes.POINTER(fe_refined_desc), ctypes.c_int,
+                                            ctypes.POINTER(fe_quad_desc), ctypes.c_double, ctypes.POINTER(_VP)]),
+        "fe_num_slaves": (ctypes.c_int, [_VP]),
+        "fe_node_coords": (ctypes.c_int, [_VP, _DP]),
         "fe_apply_scaled": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, _VP]),
         "fe_chebyshev_filter": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -191,6 +201,30 @@ def fe_setup(nx: int, ny: int, nz: int, p: int, n_q: int, *, periodic: bool = Fa
     out = _VP()
     _check(lib().fe_setup(ctypes.byref(md), p, ctypes.byref(qd), mu, ctypes.byref(out)), "fe_setup")
     return out.value
+
+
+def fe_setup_refined(nx: int, ny: int, nz: int, p: int, n_q: int, refine_lo, refine_hi, *,
+                     lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), quad: int = FE_QUAD_GAUSS, mu: float = 0.5) -> int:
+    """One-level refined Dirichlet box with hanging nodes (include/fe.h)."""
+    d = fe_refined_desc()
+    d.nx, d.ny, d.nz = nx, ny, nz
+    for k in range(3):
+        d.lo[k], d.hi[k] = float(lo[k]), float(hi[k])
+        d.refine_lo[k], d.refine_hi[k] = int(refine_lo[k]), int(refine_hi[k])
+    q = fe_quad_desc(n_q, quad)
+    out = _VP()
+    _check(lib().fe_setup_refined(ctypes.byref(d), p, ctypes.byref(q), mu, ctypes.byref(out)), "fe_setup_refined")
+    return out.value
+
+
+def fe_num_slaves(ctx: int) -> int:
+    return int(lib().fe_num_slaves(ctx))
+
+
+def fe_node_coords(ctx: int) -> np.ndarray:
+    xyz = np.zeros((fe_num_dofs(ctx), 3))
+    _check(lib().fe_node_coords(ctx, xyz.ctypes.data_as(_DP)), "fe_node_coords")
+    return xyz
 
 
 def fe_destroy(ctx: int) -> None:

@@ -168,6 +168,12 @@ WORKLOADS = {
     "e1": Workload("unit cube 17^3, p=6, n_q=8, Dirichlet-0 (1,092,727 DoFs): 1024 wanted eigenpairs, "
                    "1280-vector subspace, Chebyshev degree 67", 17, 17, 17, False, 6, 8, 1280, "normal", 8, "gauss",
                    v_seed=18, extra={"n_wanted": 1024, "degree": 67, "tol": 5e-5}),
+    # one-level adaptive refinement with hanging nodes (the paper's adaptive-mesh cases have
+    # 1.2-2.1M DoFs): coarse 14^3 unit cube, the central 8^3 coarse cells split into 2x2x2;
+    # nx/ny/nz are the coarse counts (num_dofs does not apply: ask the context)
+    "h1": Workload("unit cube 14^3 coarse cells, central 8^3 refined once (hanging nodes), p=6, n_q=8, "
+                   "Dirichlet-0, n_vec=64", 14, 14, 14, False, 6, 8, 64, "normal", 9, "gauss", v_seed=19,
+                   extra={"refine_lo": (3, 3, 3), "refine_hi": (11, 11, 11)}),
 }
 
 
