@@ -426,6 +426,41 @@ def chfsi_bench(fe, torch, fp32_switch: float = 1e-2) -> dict:
     return out
 
 
+def refined_bench(fe, torch, steps: int = 3) -> dict:
+    """The one-level refined mesh with hanging nodes (14^3 coarse cells, the
+    central 8^3 split, p = 6, 64 vectors): time per constrained product
+    (distribute, map cell kernels, condense) in FP64 and double-float."""
+    w = inputs.WORKLOADS["h1"]
+    ctx = fe.fe_setup_refined(w.nx, w.ny, w.nz, w.p, w.nq, w.extra["refine_lo"], w.extra["refine_hi"], mu=w.mu)
+    out = {"workload": w.name, "dofs": fe.fe_num_dofs(ctx), "cells": fe.fe_num_cells(ctx),
+           "hanging_nodes": fe.fe_num_slaves(ctx), "n_vec": w.n_vec}
+    try:
+        fe.fe_set_potential(ctx, w.potential_at(fe.fe_quadrature_points(ctx)))
+        n = fe.fe_num_dofs(ctx)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(w.x_seed)
+        X = torch.randn(n, w.n_vec, device="cuda", dtype=torch.float64, generator=g)
+        Y = torch.empty_like(X)
+        for mode in ("fp64", "df64"):
+            fe.fe_set_mode(ctx, mode)
+            for _ in range(3):
+                fe.fe_apply(ctx, X, Y)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(steps):
+                fe.fe_apply(ctx, X, Y)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / steps
+            out[mode] = {"ms_per_apply": ms, "value": n * w.n_vec / (ms * 1e-3) / 1e9, "unit": UNIT}
+        del X, Y
+    finally:
+        fe.fe_destroy(ctx)
+    torch.cuda.empty_cache()
+    return out
+
+
 def distorted_bench(fe, torch, steps: int = 2, rows: int = 24):
     """The perturbed 16^3, p = 8, n_vec = 256 workload (trilinear cells,
     per-point metric): time per apply and relative error against the FP64
@@ -563,6 +598,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-distorted", action="store_true")
     ap.add_argument("--no-chfsi", action="store_true")
+    ap.add_argument("--no-refined", action="store_true")
     ap.add_argument("--profile-precond", type=int, default=0, help="cells per direction of a preconditioner-only run")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -705,6 +741,8 @@ def main():
         out["distorted"] = distorted_bench(fe, torch)
     if rank == 0 and not args.no_chfsi:
         out["chfsi"] = chfsi_bench(fe, torch)
+    if rank == 0 and not args.no_refined:
+        out["refined"] = refined_bench(fe, torch)
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
