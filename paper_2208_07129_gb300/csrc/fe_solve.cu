@@ -34,10 +34,16 @@ __global__ void col_dot_partial(const T* __restrict__ a, const T* __restrict__ b
     const size_t rows_per = (n + gridDim.x - 1) / gridDim.x;
     const size_t r0 = (size_t)blockIdx.x * rows_per;
     const size_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
-    for (size_t r = r0 + threadIdx.y; r < r1; r += blockDim.y) {
-      const size_t i = r * nv + c;
+    const size_t st = blockDim.y;
+    size_t r = r0 + threadIdx.y;
+    double s2 = 0.0;
+    for (; r + st < r1; r += 2 * st) {   // two rows in flight per thread
+      const size_t i = r * nv + c, j = (r + st) * nv + c;
       s += (double)a[i] * (double)b[i];
+      s2 += (double)a[j] * (double)b[j];
     }
+    if (r < r1) s += (double)a[r * nv + c] * (double)b[r * nv + c];
+    s += s2;
   }
   red[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
@@ -95,12 +101,54 @@ __global__ void cg_update_kernel(T* __restrict__ x, T* __restrict__ r, const T* 
   }
 }
 
-// p = z + beta_c p
+// p = z + beta_c p   (column-structured like the reductions: no index division)
 template <typename T>
 __global__ void cg_direction_kernel(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta,
-                                    size_t total, int nv) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + (T)beta[i % nv] * p[i];
+                                    size_t n, int nv) {
+  const int c = blockIdx.y * kColTile + threadIdx.x;
+  if (c >= nv) return;
+  const T bc = (T)beta[c];
+  const size_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+  const size_t r0 = (size_t)blockIdx.x * rows_per;
+  const size_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
+  for (size_t r = r0 + threadIdx.y; r < r1; r += blockDim.y) {
+    const size_t i = r * nv + c;
+    p[i] = z[i] + bc * p[i];
+  }
+}
+
+// One pass of the PCG step after alpha is known (Jacobi or no preconditioner):
+//   x += alpha_c p,  r -= alpha_c q,  z = dinv .* r,  partial[b][c] = sum r.z
+// (the separate update, preconditioner and dot-product kernels read r and z
+// again; fused they stream every vector once).
+template <typename T>
+__global__ void cg_step_kernel(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
+                               const T* __restrict__ q, const T* __restrict__ dinv, const double* __restrict__ alpha,
+                               size_t n, int nv, double* __restrict__ partial) {
+  __shared__ double red[8][kColTile];
+  const int c = blockIdx.y * kColTile + threadIdx.x;
+  double s = 0.0;
+  if (c < nv) {
+    const T a = (T)alpha[c];
+    const size_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+    const size_t r0 = (size_t)blockIdx.x * rows_per;
+    const size_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
+    for (size_t row = r0 + threadIdx.y; row < r1; row += blockDim.y) {
+      const size_t i = row * nv + c;
+      x[i] += a * p[i];
+      const T rn = r[i] - a * q[i];
+      r[i] = rn;
+      const T zn = dinv ? rn * dinv[row] : rn;
+      z[i] = zn;
+      s += (double)rn * (double)zn;
+    }
+  }
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < nv) {
+    for (int k = 1; k < (int)blockDim.y; ++k) s += red[k][threadIdx.x];
+    partial[(size_t)blockIdx.x * nv + c] = s;
+  }
 }
 
 // alpha = active ? rz / pq : 0 ; flags a breakdown when pq <= 0 on an active column
@@ -276,14 +324,16 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
     if (st != FE_OK) return st;
     if ((e = col_dot<T>(p, q, n, nv, w.partial, pq, s)) != cudaSuccess) return from_cuda(e);
     cg_alpha_kernel<<<(nv + 127) / 128, 128, 0, s>>>(rz, pq, w.active, alpha, nv, c->d_status);
-    cg_update_kernel<T><<<ew_grid(tot), 256, 0, s>>>(x, r, p, q, alpha, tot, nv);
     if (learned) {
+      cg_update_kernel<T><<<ew_grid(tot), 256, 0, s>>>(x, r, p, q, alpha, tot, nv);
       st = learned_precond_apply(c, r, z, nv, sizeof(T) == 8, s);
       if (st != FE_OK) return st;
+      if ((e = col_dot<T>(r, z, n, nv, w.partial, rznew, s)) != cudaSuccess) return from_cuda(e);
     } else {
-      precond_jacobi_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv, z, n, nv);
+      const dim3 grid(kRedBlocks, (nv + kColTile - 1) / kColTile);
+      cg_step_kernel<T><<<grid, dim3(kColTile, 8), 0, s>>>(x, r, z, p, q, dinv, alpha, n, nv, w.partial);
+      col_sum_partials<<<(nv + 127) / 128, 128, 0, s>>>(w.partial, kRedBlocks, nv, rznew);
     }
-    if ((e = col_dot<T>(r, z, n, nv, w.partial, rznew, s)) != cudaSuccess) return from_cuda(e);
     if (learned) {
       fcg_safeguard_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv_all, z, rznew, tot, nv);
       if ((e = col_dot<T>(r, z, n, nv, w.partial, rznew, s)) != cudaSuccess) return from_cuda(e);
@@ -291,7 +341,8 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
       if ((e = col_dot<T>(z, q, n, nv, w.partial, rzmid, s)) != cudaSuccess) return from_cuda(e);
     }
     cg_beta_kernel<<<(nv + 127) / 128, 128, 0, s>>>(rznew, rzmid, pq, rz, w.active, beta, nv, learned ? 1 : 0);
-    cg_direction_kernel<T><<<ew_grid(tot), 256, 0, s>>>(p, z, beta, tot, nv);
+    cg_direction_kernel<T><<<dim3(kRedBlocks, (nv + kColTile - 1) / kColTile), dim3(kColTile, 8), 0, s>>>(
+        p, z, beta, n, nv);
     ++it;
     if (hook) hook(hook_user, it, x, r, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return from_cuda(e);
