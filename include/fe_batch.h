@@ -33,11 +33,14 @@ typedef struct {
 } fe_batch_info;
 
 /* Plan a batch over n contexts (each a degree 3..8 operator with n_q = p + 2
- * on affine cells; FE_EUNSUPPORTED otherwise) with fixed block widths
- * n_vec[i] > 0 (host array), in mode FE_FP64 or FE_FP32.  With autotune != 0
- * the vectors per work item of every (degree, block-width bucket) are chosen
- * by timing the candidates on a 4^3 periodic proxy mesh; otherwise a fixed
- * rule is used.  The contexts must outlive the batch.  Synchronous. */
+ * on affine cells of a structured mesh; FE_EUNSUPPORTED otherwise) with
+ * fixed block widths n_vec[i] > 0 (host array), in mode FE_FP64, FE_DF64
+ * (FP64 data, double-float arithmetic) or FE_FP32.  Every work item runs the
+ * cell body of the mode's default per-colour kernel, so results equal
+ * fe_apply's bit for bit.  With autotune != 0 the vectors per work item of
+ * every (degree, block-width bucket) are chosen by timing the candidates on
+ * an 8^3 periodic proxy mesh (at most 64 vectors); otherwise a fixed rule is
+ * used.  The contexts must outlive the batch.  Synchronous. */
 fe_status fe_batch_create(fe_ctx* const* ctxs, int n, const int* n_vec, fe_mode mode, int autotune, fe_batch** out);
 
 /* Y[i] = A_i X[i] for every problem: X, Y host arrays of n device pointers

@@ -22,10 +22,13 @@
 #include <map>
 #include <vector>
 
+#include <type_traits>
+
 #include "fe_internal.h"
 #include "fe_cell_kernel.cuh"
 #include "fe_dispatch.cuh"
 #include "fe_evenodd.cuh"
+#include "fe_ff_body.cuh"
 #include "../../include/fe_batch.h"
 
 namespace fe {
@@ -47,18 +50,29 @@ struct WorkItem {
   int problem, color, cell_begin, cell_count, vb;
 };
 
+// Element type of X and Y for a compute type (double-float computes on FP64 data).
+template <typename T>
+struct DataOf { using type = T; };
+template <>
+struct DataOf<ff> { using type = double; };
+
 // kinds: p = 3..8 with n_q = p + 2 on affine cells
 constexpr int kind_of(int p) { return p - 3; }
 
 template <typename T, int NP, int NQ>
-__device__ __forceinline__ void run_item(const BatchProblemDev<T>& P, const WorkItem& w, const T* X, T* Y, T* smem,
+__device__ __forceinline__ void run_item(const BatchProblemDev<T>& P, const WorkItem& w,
+                                         const typename DataOf<T>::type* X, typename DataOf<T>::type* Y, T* smem,
                                          const T* stab) {
   const EOTables<T, NP, NQ>& tab = *reinterpret_cast<const EOTables<T, NP, NQ>*>(stab);
   const int tid = threadIdx.x, vb = P.vb;
   const int v = tid % vb, ty = tid / vb, nty = kBatchThreads / vb;
   for (int c = 0; c < w.cell_count; ++c) {
     const int e = P.cells[w.cell_begin + c];
-    cell_body_eo<T, NP, NQ, false>(tab, P.m, P.geo, e, w.vb, vb, v, ty, nty, P.n_vec, X, Y, smem);
+    if constexpr (std::is_same<T, ff>::value)
+      cell_body_ff<NP, NQ, false, false>(tab, P.m, P.geo, e, w.vb, vb, v, ty, nty, P.n_vec, X, Y, smem,
+                                         Scale<double>{});
+    else
+      cell_body_eo<T, NP, NQ, false>(tab, P.m, P.geo, e, w.vb, vb, v, ty, nty, P.n_vec, X, Y, smem);
     __syncthreads();
   }
 }
@@ -94,8 +108,9 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchProblem
     }
     for (int k = threadIdx.x; k < kTabImage; k += blockDim.x) stab[k] = P.tab[k];
     __syncthreads();
-    const T* X = static_cast<const T*>(ptrs[2 * w.problem]);
-    T* Y = static_cast<T*>(const_cast<void*>(ptrs[2 * w.problem + 1]));
+    using D = typename DataOf<T>::type;
+    const D* X = static_cast<const D*>(ptrs[2 * w.problem]);
+    D* Y = static_cast<D*>(const_cast<void*>(ptrs[2 * w.problem + 1]));
     switch (P.kind) {
       case 0: run_item<T, 4, 5>(P, w, X, Y, smem, stab); break;
       case 1: run_item<T, 5, 6>(P, w, X, Y, smem, stab); break;
@@ -171,7 +186,7 @@ std::vector<int> candidates(int nq, int n_vec, size_t elem) {
 // block width (capped at 64 vectors) for every candidate tile; return the
 // fastest vectors-per-CTA.
 int autotune(const fe_ctx* c, int n_vec_full, fe_mode mode, float* spent_ms) {
-  const size_t elem = mode == FE_FP64 ? 8 : 4;
+  const size_t elem = mode == FE_FP32 ? 4 : 8;
   std::vector<int> cand = candidates(c->nq, n_vec_full, elem);
   if (cand.size() == 1) return cand[0];
   const int n_vec = std::min(n_vec_full, 64);
@@ -193,7 +208,7 @@ int autotune(const fe_ctx* c, int n_vec_full, fe_mode mode, float* spent_ms) {
     cudaEventCreate(&b);
     float best_ms = 1e30f;
     for (int vb : cand) {
-      fe_set_tile(px, mode, vb, kBatchThreads / vb, mode == FE_FP64 ? 0 : 3);   // the even-odd line kernel
+      fe_set_tile(px, mode, vb, kBatchThreads / vb, mode == FE_FP32 ? 3 : 0);   // the even-odd line kernel
       fe_apply(px, X, Y, n_vec, nullptr);
       cudaEventRecord(a);
       for (int r = 0; r < 3; ++r) fe_apply(px, X, Y, n_vec, nullptr);
@@ -227,7 +242,8 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
     fe_ctx* c = b->ctxs[i];
     BatchProblemDev<T>& P = hp[i];
     P.m = c->mdev;
-    if (b->mode == FE_FP64) P.geo = Geom<T>{(const T*)c->d_cellG64, (const T*)c->d_ptG64, (const T*)c->d_ptC64};
+    if constexpr (std::is_same<T, ff>::value) P.geo = Geom<ff>{c->d_cellGff, c->d_ptGff, c->d_ptCff};
+    else if (b->mode == FE_FP64) P.geo = Geom<T>{(const T*)c->d_cellG64, (const T*)c->d_ptG64, (const T*)c->d_ptC64};
     else P.geo = Geom<T>{(const T*)c->d_cellG32, (const T*)c->d_ptG32, (const T*)c->d_ptC32};
     P.n_vec = b->n_vec[i];
     P.kind = kind_of(c->p);
@@ -331,7 +347,7 @@ extern "C" fe_status fe_batch_create(fe_ctx* const* ctxs, int n, const int* n_ve
   if (!out) return FE_EINVAL;
   *out = nullptr;
   if (!ctxs || !n_vec || n <= 0) return FE_EINVAL;
-  if (mode != FE_FP64 && mode != FE_FP32) return FE_EUNSUPPORTED;
+  if (mode != FE_FP64 && mode != FE_FP32 && mode != FE_DF64) return FE_EUNSUPPORTED;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || n_vec[i] <= 0) return FE_EINVAL;
     if (ctxs[i]->general || ctxs[i]->refined || ctxs[i]->p < 3 || ctxs[i]->p > 8 || ctxs[i]->nq != ctxs[i]->p + 2)
@@ -344,7 +360,9 @@ extern "C" fe_status fe_batch_create(fe_ctx* const* ctxs, int n, const int* n_ve
   b->n_vec.assign(n_vec, n_vec + n);
   b->vb.assign(n, 0);
   b->cells_per_item.assign(n, 1);
-  fe_status st = mode == FE_FP64 ? build_batch<double>(b, autotune_on) : build_batch<float>(b, autotune_on);
+  fe_status st = mode == FE_FP64 ? build_batch<double>(b, autotune_on)
+                 : mode == FE_DF64 ? build_batch<ff>(b, autotune_on)
+                                   : build_batch<float>(b, autotune_on);
   if (st != FE_OK) {
     fe_batch_destroy(b);
     return st;
