@@ -37,7 +37,10 @@ typedef struct {
  * fixed block widths n_vec[i] > 0 (host array), in mode FE_FP64, FE_DF64
  * (FP64 data, double-float arithmetic) or FE_FP32.  Every work item runs the
  * cell body of the mode's default per-colour kernel, so results equal
- * fe_apply's bit for bit.  With autotune != 0 the vectors per work item of
+ * fe_apply's bit for bit.  FE_FP64 runs one persistent kernel over all
+ * problems; FE_DF64 and FE_FP32 run one persistent kernel per degree (its
+ * tables as kernel parameters, its own queue) as parallel branches of the
+ * graph.  All problems of one degree must use the same quadrature rule.  With autotune != 0 the vectors per work item of
  * every (degree, block-width bucket) are chosen by timing the candidates on
  * an 8^3 periodic proxy mesh (at most 64 vectors); otherwise a fixed rule is
  * used.  The contexts must outlive the batch.  Synchronous. */

@@ -36,6 +36,7 @@ namespace fe {
 constexpr int kBatchThreads = 128;
 constexpr int kMaxColors = 27;
 constexpr int kTabImage = 256;   // elements of an EOTables<T, NP, NQ> image (195 at p = 8, n_q = 10)
+constexpr int kKinds = 6;        // degrees 3..8 with n_q = p + 2
 
 template <typename T>
 struct BatchProblemDev {
@@ -62,8 +63,7 @@ constexpr int kind_of(int p) { return p - 3; }
 template <typename T, int NP, int NQ>
 __device__ __forceinline__ void run_item(const BatchProblemDev<T>& P, const WorkItem& w,
                                          const typename DataOf<T>::type* X, typename DataOf<T>::type* Y, T* smem,
-                                         const T* stab) {
-  const EOTables<T, NP, NQ>& tab = *reinterpret_cast<const EOTables<T, NP, NQ>*>(stab);
+                                         const EOTables<T, NP, NQ>& tab) {
   const int tid = threadIdx.x, vb = P.vb;
   const int v = tid % vb, ty = tid / vb, nty = kBatchThreads / vb;
   for (int c = 0; c < w.cell_count; ++c) {
@@ -77,12 +77,67 @@ __device__ __forceinline__ void run_item(const BatchProblemDev<T>& P, const Work
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchProblemDev<T>* __restrict__ probs,
+// One persistent kernel per degree (the problems of that degree, their own
+// queue): each instantiation gets the registers its cell body needs instead
+// of those of the largest degree in the batch, and the degree's 1D tables
+// (the same for all its problems) travel as a kernel parameter, so the
+// contractions read their coefficients from the constant bank as in the
+// per-colour kernels.
+template <typename T, int NP, int NQ>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const EOTables<T, NP, NQ> tab,
+                                                             const BatchProblemDev<T>* __restrict__ probs,
                                                              const void* const* __restrict__ ptrs,
                                                              const WorkItem* __restrict__ items, int n_items,
                                                              int* next, int* done, const int* __restrict__ need,
                                                              int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const WorkItem w = items[it];
+    const BatchProblemDev<T>& P = probs[w.problem];
+    if (threadIdx.x == 0 && w.color > 0) {
+      const int idx = w.problem * kMaxColors + w.color - 1;
+      long long spins = 0;
+      while (atomicAdd(&done[idx], 0) < need[idx]) {
+        __nanosleep(128);
+        if (++spins > (1LL << 26)) {
+          atomicMax(status, (int)FE_ETIMEOUT);
+          break;
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    using D = typename DataOf<T>::type;
+    const D* X = static_cast<const D*>(ptrs[2 * w.problem]);
+    D* Y = static_cast<D*>(const_cast<void*>(ptrs[2 * w.problem + 1]));
+    run_item<T, NP, NQ>(P, w, X, Y, smem, tab);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&done[w.problem * kMaxColors + w.color], 1);
+    }
+    __syncthreads();
+  }
+}
+
+
+// FP64: one persistent kernel for every degree, the tables of each item's
+// problem staged in shared memory.  Measured faster than the per-degree
+// kernels for FP64 (950 against 1030 ms on the 24-problem batch): the FP64
+// pipe bounds both, and one kernel keeps every degree's work in flight
+// together.  Its register allocation is the largest degree's, which costs the
+// double-float and FP32 cell bodies much more than it costs FP64.
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel_all(const BatchProblemDev<T>* __restrict__ probs,
+                                                                 const void* const* __restrict__ ptrs,
+                                                                 const WorkItem* __restrict__ items, int n_items,
+                                                                 int* next, int* done, const int* __restrict__ need,
+                                                                 int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) T stab[kTabImage];
   __shared__ int s_item;
@@ -111,15 +166,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchProblem
     using D = typename DataOf<T>::type;
     const D* X = static_cast<const D*>(ptrs[2 * w.problem]);
     D* Y = static_cast<D*>(const_cast<void*>(ptrs[2 * w.problem + 1]));
+#define FE_ITEM(K, NP, NQ) \
+  case K: run_item<T, NP, NQ>(P, w, X, Y, smem, *reinterpret_cast<const EOTables<T, NP, NQ>*>(stab)); break;
     switch (P.kind) {
-      case 0: run_item<T, 4, 5>(P, w, X, Y, smem, stab); break;
-      case 1: run_item<T, 5, 6>(P, w, X, Y, smem, stab); break;
-      case 2: run_item<T, 6, 7>(P, w, X, Y, smem, stab); break;
-      case 3: run_item<T, 7, 8>(P, w, X, Y, smem, stab); break;
-      case 4: run_item<T, 8, 9>(P, w, X, Y, smem, stab); break;
-      case 5: run_item<T, 9, 10>(P, w, X, Y, smem, stab); break;
+      FE_ITEM(0, 4, 5) FE_ITEM(1, 5, 6) FE_ITEM(2, 6, 7) FE_ITEM(3, 7, 8) FE_ITEM(4, 8, 9) FE_ITEM(5, 9, 10)
       default: break;
     }
+#undef FE_ITEM
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(&done[w.problem * kMaxColors + w.color], 1);
@@ -140,12 +193,15 @@ struct fe_batch {
   void* d_probs = nullptr;
   WorkItem* d_items = nullptr;
   int n_items = 0, n_phases = 0;
+  int item_begin[kKinds + 1] = {0};   // items of degree kind k: [item_begin[k], item_begin[k + 1])
   int *d_next = nullptr, *d_done = nullptr, *d_need = nullptr, *d_status = nullptr;
   const void** h_ptrs = nullptr;   // pinned host staging of the X / Y table
   void** d_ptrs = nullptr;
   size_t smem = 0;
   int grid = 0;
   cudaStream_t cap = nullptr;
+  cudaStream_t side[kKinds] = {};       // one capture branch per degree
+  cudaEvent_t fork = nullptr, join[kKinds] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   float tune_ms = 0.f;
@@ -229,6 +285,31 @@ int autotune(const fe_ctx* c, int n_vec_full, fe_mode mode, float* spent_ms) {
   return best;
 }
 
+// Capture the persistent kernel of one degree: grid = its occupancy x SMs
+// (at most one CTA per work item).
+template <typename T, int NP, int NQ>
+cudaError_t launch_kind(fe_batch* b, int kind, int n_k, size_t smem) {
+  auto kern = batch_kernel<T, NP, NQ>;
+  const fe_ctx* c0 = nullptr;   // the degree's tables: those of its first problem (all equal)
+  for (int i = 0; i < b->n && !c0; ++i)
+    if (kind_of(b->ctxs[i]->p) == kind) c0 = b->ctxs[i];
+  if (!c0) return cudaErrorInvalidValue;
+  const EOTables<T, NP, NQ> tab = make_eotables<T, NP, NQ>(c0);
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
+  if (e != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int grid = std::max(1, std::min(n_k, std::max(1, per_sm) * sms));
+  b->grid = std::max(b->grid, grid);
+  kern<<<grid, kBatchThreads, smem, b->side[kind]>>>(tab, static_cast<const BatchProblemDev<T>*>(b->d_probs),
+                                              const_cast<const void* const*>(b->d_ptrs),
+                                              b->d_items + b->item_begin[kind], n_k, b->d_next + kind, b->d_done,
+                                              b->d_need, b->d_status);
+  return cudaGetLastError();
+}
+
 template <typename T>
 fe_status build_batch(fe_batch* b, int autotune_on) {
   const int n = b->n;
@@ -276,14 +357,18 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
     }
     smem = std::max(smem, tile_smem<T>(c->nq, vb));
   }
-  // work items, phase-major
+  // work items, phase-major: one queue over all problems (FP64, merged
+  // kernel) or one queue per degree (per-degree kernels)
+  constexpr bool merged = std::is_same<T, double>::value;
   std::vector<WorkItem> items;
   int phases = 0;
+  for (int kind = 0; kind < (merged ? 1 : kKinds); ++kind) {
+  b->item_begin[kind] = (int)items.size();
   for (int k = 0; k < kMaxColors; ++k) {
     bool any = false;
     for (int i = 0; i < n; ++i) {
       fe_ctx* c = b->ctxs[i];
-      if (k >= c->colors.n_colors) continue;
+      if ((!merged && hp[i].kind != kind) || k >= c->colors.n_colors) continue;
       any = true;
       const int c0 = c->colors.offset[k], c1 = c->colors.offset[k + 1];
       const BatchProblemDev<T>& P = hp[i];
@@ -298,8 +383,10 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
           need[(size_t)i * kMaxColors + k]++;
         }
     }
-    if (any) phases = k + 1;
+    if (any) phases = std::max(phases, k + 1);
   }
+  }
+  for (int kind = merged ? 1 : kKinds; kind <= kKinds; ++kind) b->item_begin[kind] = (int)items.size();
   b->n_items = (int)items.size();
   b->n_phases = phases;
   b->smem = smem;
@@ -311,30 +398,59 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
   if (e == cudaSuccess) e = cudaMalloc(&b->d_need, need.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_done, need.size() * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_next, kKinds * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, 2 * n * sizeof(void*));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_ptrs, 2 * n * sizeof(void*));
-  if (e == cudaSuccess && smem > 48 * 1024)
-    e = cudaFuncSetAttribute(batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<T>, kBatchThreads, smem);
   if (e != cudaSuccess) return from_cuda(e);
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  b->grid = std::max(1, std::min(b->n_items, std::max(1, per_sm) * sms));
-  // graph: reset the queue and the colour counters, then the persistent kernel
+  // graph: reset the queues and the colour counters, then one persistent
+  // kernel per degree present, as parallel branches (the degrees share the
+  // GPU, and one degree's tail overlaps the others' work).  Every wait of a
+  // CTA is on items its own kernel dequeued earlier, whose CTAs are running,
+  // so concurrent branches cannot block each other.
   e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int k = 0; k < kKinds && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int k = 0; k < kKinds && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaMemsetAsync(b->d_next, 0, sizeof(int), b->cap);
+    cudaMemsetAsync(b->d_next, 0, kKinds * sizeof(int), b->cap);
     cudaMemsetAsync(b->d_done, 0, need.size() * sizeof(int), b->cap);
-    batch_kernel<T><<<b->grid, kBatchThreads, smem, b->cap>>>(
-        static_cast<const BatchProblemDev<T>*>(b->d_probs), const_cast<const void* const*>(b->d_ptrs), b->d_items,
-        b->n_items, b->d_next, b->d_done, b->d_need, b->d_status);
-    e = cudaStreamEndCapture(b->cap, &b->graph);
+    cudaEventRecord(b->fork, b->cap);
+    if constexpr (merged) {
+      auto kern = batch_kernel_all<T>;
+      if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int per_sm = 0, sms = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+      b->grid = std::max(1, std::min(b->n_items, std::max(1, per_sm) * sms));
+      if (e == cudaSuccess)
+        kern<<<b->grid, kBatchThreads, smem, b->cap>>>(static_cast<const BatchProblemDev<T>*>(b->d_probs),
+                                                       const_cast<const void* const*>(b->d_ptrs), b->d_items,
+                                                       b->n_items, b->d_next, b->d_done, b->d_need, b->d_status);
+    }
+    for (int kind = 0; kind < kKinds && e == cudaSuccess && !merged; ++kind) {
+      const int n_k = b->item_begin[kind + 1] - b->item_begin[kind];
+      if (n_k == 0) continue;
+      e = cudaStreamWaitEvent(b->side[kind], b->fork, 0);
+      if (e != cudaSuccess) break;
+      switch (kind) {
+        case 0: e = launch_kind<T, 4, 5>(b, kind, n_k, smem); break;
+        case 1: e = launch_kind<T, 5, 6>(b, kind, n_k, smem); break;
+        case 2: e = launch_kind<T, 6, 7>(b, kind, n_k, smem); break;
+        case 3: e = launch_kind<T, 7, 8>(b, kind, n_k, smem); break;
+        case 4: e = launch_kind<T, 8, 9>(b, kind, n_k, smem); break;
+        case 5: e = launch_kind<T, 9, 10>(b, kind, n_k, smem); break;
+        default: break;
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(b->join[kind], b->side[kind]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[kind], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    b->graph = g;
+    if (e == cudaSuccess) e = e2;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   return from_cuda(e);
@@ -352,6 +468,8 @@ extern "C" fe_status fe_batch_create(fe_ctx* const* ctxs, int n, const int* n_ve
     if (!ctxs[i] || n_vec[i] <= 0) return FE_EINVAL;
     if (ctxs[i]->general || ctxs[i]->refined || ctxs[i]->p < 3 || ctxs[i]->p > 8 || ctxs[i]->nq != ctxs[i]->p + 2)
       return FE_EUNSUPPORTED;
+    for (int j = 0; j < i; ++j)   // one quadrature rule per degree: the degree's kernel carries one set of tables
+      if (ctxs[j]->p == ctxs[i]->p && ctxs[j]->quad_kind != ctxs[i]->quad_kind) return FE_EUNSUPPORTED;
   }
   fe_batch* b = new fe_batch();
   b->n = n;
@@ -409,6 +527,11 @@ extern "C" void fe_batch_destroy(fe_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int k = 0; k < kKinds; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   cudaFree(b->d_probs); cudaFree(b->d_items); cudaFree(b->d_need); cudaFree(b->d_done); cudaFree(b->d_next);
   cudaFree(b->d_status); cudaFree(b->d_ptrs);
   if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
