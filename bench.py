@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -37,7 +38,7 @@ UNIT = "GDoF-vectors/s"
 # Roofline denominators.  HBM: measured copy bandwidth.  ALU-bound kernels: the
 # pipe's unit count times the maximum SM clock (GB300: 152 SMs; per SM and clock
 # 2 FP64 FMA lanes -- a DFMA microbenchmark measured 1.19 TFLOP/s -- and 128 FP32
-# FMA lanes), see the design doc.
+# FMA lanes).
 SMS = 152
 
 
@@ -78,7 +79,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples go to FE_BENCH_OUT (default: the system temporary directory)
+        out_dir = os.environ.get("FE_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -290,7 +293,7 @@ def time_mode(fe, torch, ctx, w, mode, steps, warmup, world):
 
 
 def solve_bench(fe, torch, sub_cols: int = 16, cpu: bool = True):
-    """Time to relative residual 1e-8 (FP64 operator as judge) for the block
+    """Time to relative residual 1e-8 (checked with the FP64 operator) for the block
     PCG solve of the 24^3, p=6, 128-column problem: mixed precision (FP32 inner
     PCG with Jacobi, FP64 refinement) run to the end, and FP64 Jacobi-PCG
     extrapolated from a full solve of `sub_cols` columns (its iteration count)

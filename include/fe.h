@@ -238,7 +238,7 @@ typedef struct {
  * X's boundary rows stay 0.
  *   inner_mode == FE_FP64: PCG in FP64.
  *   inner_mode == FE_DF64: PCG in FP64 with the double-float operator
- *   (FE_DF64); the FP64 operator judges the result.
+ *   (FE_DF64); the FP64 operator checks the result.
  *   otherwise (FE_FP32/TF32/BF16/TF32X3): FP64 iterative refinement -- r = B - A X with the FP64
  *   operator, an inner PCG in inner_mode (FP32 data; FE_FP32/TF32/BF16/TF32X3
  *   operator) on r / ||r|| to the relative reduction still needed

@@ -454,14 +454,14 @@ extern "C" fe_status fe_solve(fe_ctx* c, const double* B, double* X, int nv, dou
   if (inner_mode == FE_FP64 || inner_mode == FE_DF64) {
     // FP64 PCG (operator in FP64, or in double-float arithmetic for
     // FE_DF64); the recurrence residual is trusted to rtol/2, then the FP64
-    // operator judges.
+    // operator checks the result.
     for (int j = 0; j < nv; ++j) tol[j] = 0.5 * rtol * bnorm[j];
     int its = 0;
     c->op64 = (fe_mode)inner_mode;
     st = pcg<double>(c, B, X, nv, tol.data(), max_it, precond, s, w.v64[0], w.v64[1], w.v64[2], w.v64[3], &its, 1);
     c->op64 = FE_FP64;
     inf.iterations = its;
-    fp64_applies = inner_mode == FE_FP64 ? its + 1 : 0;   // the judge below adds one
+    fp64_applies = inner_mode == FE_FP64 ? its + 1 : 0;   // the final check below adds one
   } else {
     // FP64 iterative refinement: r = b - A64 x; solve A32 d = r / ||r|| in the
     // inner precision to the reduction still needed (rtol ||b|| / ||r||), but

@@ -98,7 +98,7 @@ def test_training_gain_over_jacobi(fe):
     """Train on a 12^3, p=6 problem (V + sigma as in the block-PCG workload;
     energy-norm objective, checkpoint picked on held-out right-hand sides),
     then solve 16 fresh right-hand sides with the mixed-precision block PCG:
-    Jacobi vs the learned preconditioner, both judged by the FP64 operator."""
+    Jacobi vs the learned preconditioner, both checked with the FP64 operator."""
     w = inputs.Workload("12^3 p=6", 12, 12, 12, False, 6, 8, 16, "normal", 77, "gauss", v_seed=15, v_amp=0.125,
                         v_shift=1.0)
     ctx = fe.setup_workload(w)

@@ -55,7 +55,7 @@ def test_pcg_solution(fe, precond, inner):
         err = np.linalg.norm(X - Xref) / np.linalg.norm(Xref)
         assert err < 1e-6, err
         if inner == "df64":
-            # FP64 PCG on the double-float operator: only the judge is an FP64 apply
+            # FP64 PCG on the double-float operator: only the final check is an FP64 apply
             assert res["outer_iterations"] == 0 and res["fp64_applies"] == 1
         elif inner != "fp64":
             # FP64 refinement around the reduced-precision inner solve: one FP64
