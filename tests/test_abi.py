@@ -78,3 +78,21 @@ def test_eig_layer_null_arguments(libfe):
     assert L.fe_apply_scaled(None, None, None, 1, 1.0, 0.0, 0.0, None) == fe.FE_EINVAL
     assert L.fe_chebyshev_filter(None, None, None, 1, 4, 0.0, 1.0, 2.0, None) == fe.FE_EINVAL
     assert L.fe_chfsi(None, None, 4, None, None, None, None, None) == fe.FE_EINVAL
+
+
+def test_refined_mesh_calls_reject_bad_arguments(libfe):
+    from paper_2208_07129_gb300 import fe
+    L = fe.lib()
+    assert L.fe_num_slaves(None) == 0
+    assert L.fe_node_coords(None, None) == fe.FE_EINVAL
+    assert L.fe_setup_refined(None, 2, None, 0.5, None) == fe.FE_EINVAL
+    # a refinement box outside the coarse grid is rejected before any device work
+    d = fe.fe_refined_desc()
+    d.nx = d.ny = d.nz = 2
+    for k in range(3):
+        d.hi[k] = 1.0
+        d.refine_lo[k], d.refine_hi[k] = 0, 3
+    q = fe.fe_quad_desc(4, fe.FE_QUAD_GAUSS)
+    out = ctypes.c_void_p()
+    assert L.fe_setup_refined(ctypes.byref(d), 2, ctypes.byref(q), 0.5, ctypes.byref(out)) == fe.FE_EINVAL
+    assert out.value is None
