@@ -161,7 +161,12 @@ fe_mode fe_get_mode(const fe_ctx* ctx);
 /* Y = A X for n_vec >= 0 vectors (Algorithm 2 per cell, batched over cells and
  * vector blocks as in Algorithm 4, assembled without atomics by cell colours).
  * X, Y: device, num_dofs x n_vec, dtype of the current mode, X != Y (no
- * overlap).  Y is overwritten, never accumulated.  Asynchronous on stream. */
+ * overlap).  Y is overwritten, never accumulated.  Asynchronous on stream.
+ * On a refined mesh with hanging nodes the product first distributes X into a
+ * context-owned device block of X's size (X with the slave rows filled in);
+ * the first call with a given or larger n_vec allocates that block
+ * (cudaMalloc, which synchronises the device), later calls reuse it.
+ * fe_apply_host_noalloc takes the block from its fixed array instead. */
 fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream);
 
 /* Launch shape of the CUDA-core cell kernels of one mode (the autotuner's
@@ -201,8 +206,14 @@ fe_status fe_apply_host(fe_ctx* ctx, const void* X_host, void* Y_host, int n_vec
  * file-scope device array of FE_NOALLOC_STAGE_BYTES that every GPU loading
  * the library holds until the process exits; the call itself performs no
  * cudaMalloc, cudaFree or other allocation.  Limits and caveats:
- *  - 2 * num_dofs * n_vec * sizeof(element) (rounded up to 256 bytes for X)
- *    must fit in FE_NOALLOC_STAGE_BYTES, else FE_EINVAL before any copy;
+ *  - the staged blocks must fit in FE_NOALLOC_STAGE_BYTES, else FE_EINVAL
+ *    before any copy: with b = num_dofs * n_vec * sizeof(element) and
+ *    b' = b rounded up to 256 bytes, b' + b for X and Y, and 2 b' + b on a
+ *    refined mesh with hanging nodes (fe_setup_refined), whose product also
+ *    stages a copy of X with the slave rows filled in;
+ *  - modes fe_apply rejects on the context are rejected with the same status;
+ *    if the product fails after the copy of X_host was queued, the call
+ *    synchronises `stream` before returning, so no copy is left in flight;
  *  - the first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress with that device current) and caches it; make
  *    that first call before any stream capture;
@@ -211,6 +222,10 @@ fe_status fe_apply_host(fe_ctx* ctx, const void* X_host, void* Y_host, int n_vec
  *    must be serialised by the caller.  Nothing in the array needs to start
  *    at zero: X is copied in whole and Y written whole on every call. */
 fe_status fe_apply_host_noalloc(fe_ctx* ctx, const void* X_host, void* Y_host, int n_vec, void* stream);
+
+/* FE_NOALLOC_STAGE_BYTES as compiled into the library (the size of the fixed
+ * staging array of fe_apply_host_noalloc). */
+size_t fe_noalloc_stage_bytes(void);
 
 /* diag(A) as a device FP64 vector of num_dofs entries (constrained rows get 1,
  * the convention of the Jacobi preconditioner), computed matrix-free from the

@@ -74,11 +74,9 @@ cudaError_t launch_eo_map(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaStre
   if (vb * nty > 256) nty = 256 / vb;
   while ((vb * nty) % 32 != 0 && vb * nty < 256) ++nty;
   const size_t smem = (size_t)3 * NQ * NQ * NQ * vb * sizeof(T);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   const EOTables<T, NP, NQ> tab = make_eotables<T, NP, NQ>(c);
   const Geom<T> geo = make_geom<T>(c);
@@ -115,12 +113,13 @@ cudaError_t cells_refined(const fe_ctx* c, const void* X, void* Y, int n_vec, cu
 }
 
 template <typename T, typename W>
-cudaError_t constrained(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s, const W* sl_w, const W* ma_w) {
+cudaError_t constrained(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s, const W* sl_w, const W* ma_w,
+                        void* xc) {
   const size_t n = c->n_dofs, tot = n * (size_t)n_vec;
   const void* Xin = X;
   if (c->n_slaves > 0) {
     const size_t bytes = tot * sizeof(T);
-    if (c->xc_bytes < bytes) {
+    if (!xc && c->xc_bytes < bytes) {
       cudaFree(c->d_xc);
       c->d_xc = nullptr;
       c->xc_bytes = 0;
@@ -128,10 +127,11 @@ cudaError_t constrained(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream
       if (e != cudaSuccess) return e;
       c->xc_bytes = bytes;
     }
+    if (!xc) xc = c->d_xc;
     const unsigned grid = (unsigned)std::min<size_t>((tot + 255) / 256, 152 * 16);
-    distribute_kernel<T, W><<<grid, 256, 0, s>>>(static_cast<const T*>(X), static_cast<T*>(c->d_xc), c->d_row_slave,
+    distribute_kernel<T, W><<<grid, 256, 0, s>>>(static_cast<const T*>(X), static_cast<T*>(xc), c->d_row_slave,
                                                  c->d_sl_ptr, c->d_sl_idx, sl_w, n, n_vec);
-    Xin = c->d_xc;
+    Xin = xc;
   }
   cudaError_t e = cells_refined(c, Xin, Y, n_vec, s);
   if (e != cudaSuccess) return e;
@@ -150,9 +150,9 @@ cudaError_t constrained(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream
 
 }  // namespace
 
-cudaError_t apply_refined(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s) {
-  if (c->mode == FE_FP32) return constrained<float, float>(c, X, Y, n_vec, s, c->d_sl_w32, c->d_ma_w32);
-  return constrained<double, double>(c, X, Y, n_vec, s, c->d_sl_w, c->d_ma_w);
+cudaError_t apply_refined(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s, void* xc_scratch) {
+  if (c->mode == FE_FP32) return constrained<float, float>(c, X, Y, n_vec, s, c->d_sl_w32, c->d_ma_w32, xc_scratch);
+  return constrained<double, double>(c, X, Y, n_vec, s, c->d_sl_w, c->d_ma_w, xc_scratch);
 }
 
 }  // namespace fe

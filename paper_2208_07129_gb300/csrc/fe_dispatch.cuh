@@ -51,11 +51,9 @@ cudaError_t launch_apply(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaStrea
   if (vb * nty > 256) nty = 256 / vb;
   while ((vb * nty) % 32 != 0 && vb * nty < 256) ++nty;
   const size_t smem = (size_t)3 * NQ * NQ * NQ * vb * sizeof(T);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   const Tables<T, NP, NQ> tab = make_tables<T, NP, NQ>(c);
   const Geom<T> geo = make_geom<T>(c);

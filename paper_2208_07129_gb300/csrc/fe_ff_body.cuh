@@ -267,11 +267,9 @@ cudaError_t launch_df64(const fe_ctx* c, const double* X, double* Y, int n_vec, 
   if (vb * nty > 256) nty = 256 / vb;
   while ((vb * nty) % 32 != 0 && vb * nty < 256) ++nty;
   const size_t smem = (size_t)3 * NQ * NQ * NQ * vb * sizeof(ff);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   const EOTables<ff, NP, NQ> tab = make_eotables<ff, NP, NQ>(c);
   const Geom<ff> geo{c->d_cellGff, c->d_ptGff, c->d_ptCff};

@@ -160,6 +160,11 @@ struct fe_ctx {
 };
 
 namespace fe {
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on the
+// current device.  The attribute belongs to the kernel as loaded on one
+// device, so the highest value set is remembered per (kernel, device); the
+// cache is guarded by a mutex, so host threads may launch concurrently.
+cudaError_t ensure_dyn_smem(const void* kern, size_t smem);
 // Kernel dispatch (defined in the kernel translation units).
 cudaError_t apply_cc_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s);
 cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);
@@ -181,7 +186,9 @@ cudaError_t upload_doubles(double** dst, const std::vector<double>& src);
 cudaError_t upload_floats(float** dst, const std::vector<double>& src);
 cudaError_t upload_ffs(ff** dst, const std::vector<double>& src);
 // Refined meshes with hanging nodes (fe_refined.cu / fe_apply_refined.cu).
-cudaError_t apply_refined(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s);
+// xc_scratch: device block of X's size for the distribute step (X with the
+// slave rows filled in); NULL = the context's own, allocated on first use.
+cudaError_t apply_refined(fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s, void* xc_scratch = nullptr);
 void free_refined(fe_ctx* c);
 // GLL diagonal mass of Sec. 4.3 into c->mass (host, FP64; constrained rows 1).
 void build_gll_mass(fe_ctx* c);

@@ -789,12 +789,8 @@ fe_status precond_apply_f32(fe_ctx* c, const float* r, float* z, int nv, cudaStr
   const size_t n = c->n_dofs;
   jacobi_init_kernel<<<grid_for(n * nv), 256, 0, s>>>(r, c->ws.dinv32, z, n, nv);
   const size_t smem = smem_bytes(L->K1);
-  static size_t configured = 0;
-  if (smem > configured) {
-    e = cudaFuncSetAttribute(mlp_precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return from_cuda(e);
-    configured = smem;
-  }
+  e = ensure_dyn_smem(reinterpret_cast<const void*>(mlp_precond_kernel), smem);
+  if (e != cudaSuccess) return from_cuda(e);
   MlpArgs a{L->W1img, L->W2img, L->b1, L->b2, L->n3, L->K1, c->np};
   const int n_cb = (nv + kTile - 1) / kTile;
   for (int k = 0; k < c->colors.n_colors; ++k) {

@@ -404,11 +404,9 @@ cudaError_t launch_mma(const fe_ctx* c, const float* X, float* Y, int n_vec, cud
   auto kern = mma_apply_kernel<NP, NQ, GEN, KIND>;
   const size_t smem = (size_t)3 * NQ * NQ * NQ * kMmaVB * sizeof(float);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   const Tables<float, NP, NQ> tab = make_tables<float, NP, NQ>(c);
   const Geom<float> geo = make_geom<float>(c);

@@ -12,6 +12,10 @@
 // In host code the array's name stands for a host-side shadow, not for device
 // memory; its device address is obtained once per device with
 // cudaGetSymbolAddress (with that device current) and cached here.
+//
+// On a refined mesh with hanging nodes the product first writes a copy of X
+// with the slave rows filled in; that block comes from the same array, so
+// such a call needs room for three blocks instead of two.
 #include <mutex>
 
 #include "fe_internal.h"
@@ -45,26 +49,47 @@ cudaError_t stage_address(void** out) {
 
 }  // namespace
 
+extern "C" size_t fe_noalloc_stage_bytes(void) { return kFeNoAllocStageBytes; }
+
 extern "C" fe_status fe_apply_host_noalloc(fe_ctx* c, const void* Xh, void* Yh, int n_vec, void* stream) {
   if (!c || n_vec < 0) return FE_EINVAL;
   if (n_vec == 0) return FE_OK;
   if (!Xh || !Yh) return FE_EINVAL;
+  // refuse what fe_apply would refuse before any copy is queued
+  if (c->refined && c->mode != FE_FP64 && c->mode != FE_DF64 && c->mode != FE_FP32) return FE_EUNSUPPORTED;
   const size_t elem = (c->mode == FE_FP64 || c->mode == FE_DF64) ? sizeof(double) : sizeof(float);
   const size_t bytes = c->n_dofs * (size_t)n_vec * elem;
-  // X and Y both live in the array, Y at the next 256-byte boundary after X
-  const size_t y_off = (bytes + 255) / 256 * 256;
-  if (y_off + bytes > kFeNoAllocStageBytes) return FE_EINVAL;
+  // X, Y and (on a refined mesh with hanging nodes) the distribute step's copy
+  // of X with the slave rows filled in, each block at a 256-byte boundary
+  const size_t slot = (bytes + 255) / 256 * 256;
+  const int blocks = (c->refined && c->n_slaves > 0) ? 3 : 2;
+  if ((size_t)(blocks - 1) * slot + bytes > kFeNoAllocStageBytes) return FE_EINVAL;
   void* base = nullptr;
   cudaError_t e = stage_address(&base);
   if (e != cudaSuccess) return FE_ECUDA;
   char* dX = static_cast<char*>(base);
-  char* dY = dX + y_off;
+  char* dY = dX + slot;
+  char* dXc = blocks == 3 ? dX + 2 * slot : nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   e = cudaMemcpyAsync(dX, Xh, bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return FE_ECUDA;
-  fe_status st = fe_apply(c, dX, dY, n_vec, stream);
-  if (st != FE_OK) return st;
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    return FE_ECUDA;
+  }
+  fe_status st;
+  if (c->refined) {
+    e = fe::apply_refined(c, dX, dY, n_vec, s, dXc);
+    st = e == cudaSuccess ? FE_OK : FE_ECUDA;
+  } else {
+    st = fe_apply(c, dX, dY, n_vec, stream);
+  }
+  if (st != FE_OK) {
+    // the copy of the caller's X may still be in flight: let it finish before
+    // the caller reuses the buffer or another call touches the array
+    cudaStreamSynchronize(s);
+    return st;
+  }
   e = cudaMemcpyAsync(Yh, dY, bytes, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return e == cudaSuccess ? FE_OK : FE_ECUDA;
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? FE_OK : FE_ECUDA;
 }

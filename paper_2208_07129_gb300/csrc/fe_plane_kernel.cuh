@@ -230,11 +230,9 @@ template <int NP, int NQ, bool GEN>
 cudaError_t launch_plane(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s) {
   auto kern = plane_apply_kernel<NP, NQ, GEN>;
   const size_t smem = (size_t)(NP * NQ * NQ + 2 * NQ * NQ * NQ) * 32 * sizeof(float);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   const Tables<float, NP, NQ> tab = make_tables<float, NP, NQ>(c);
   const Geom<float> geo = make_geom<float>(c);

@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
         "fe_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
         "fe_apply_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
         "fe_apply_host_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+        "fe_noalloc_stage_bytes": (ctypes.c_size_t, []),
         "fe_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
         "fe_last_device_status": (ctypes.c_int, [_VP]),
         "fe_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -292,27 +293,60 @@ def fe_apply(ctx: int, X, Y, stream=None) -> None:
     _check(lib().fe_apply(ctx, X.data_ptr(), Y.data_ptr(), X.shape[1], _stream_ptr(stream)), "fe_apply")
 
 
+def _host_blocks(ctx: int, X, Y) -> int:
+    """Check a pair of host blocks for the host-buffer applies and return
+    n_vec: torch CPU tensors or numpy arrays of the context's element type
+    (float64 in FE_FP64 / FE_DF64 mode, float32 otherwise), C-contiguous,
+    2-D (num_dofs, n_vec), X and Y of the same shape.  The library reads and
+    writes exactly num_dofs * n_vec elements through the raw pointers, so a
+    mismatch here would be an out-of-bounds host access there."""
+    import torch
+    mode = fe_get_mode(ctx)
+    want = np.float64 if mode in (FE_FP64, FE_DF64) else np.float32
+    n = fe_num_dofs(ctx)
+    shapes = []
+    for a, nm in ((X, "X"), (Y, "Y")):
+        if isinstance(a, torch.Tensor):
+            ok = (not a.is_cuda and a.dtype == (torch.float64 if want is np.float64 else torch.float32)
+                  and a.is_contiguous())
+        elif isinstance(a, np.ndarray):
+            ok = a.dtype == want and a.flags["C_CONTIGUOUS"]
+        else:
+            ok = False
+        if not ok or a.ndim != 2 or a.shape[0] != n:
+            raise ValueError(f"{nm}: need a C-contiguous host {np.dtype(want).name} block of shape "
+                             f"(num_dofs={n}, n_vec)")
+        shapes.append(tuple(a.shape))
+    if shapes[0] != shapes[1]:
+        raise ValueError(f"X and Y must have the same shape, got {shapes[0]} and {shapes[1]}")
+    return shapes[0][1]
+
+
+def _host_ptr(a) -> int:
+    import torch
+    return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+
 def fe_apply_host(ctx: int, X, Y, stream=None) -> None:
     """Y = A X with host buffers (pinned torch CPU tensors or numpy arrays)."""
-    import torch
-    def ptr(a):
-        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
-    n_vec = X.shape[1]
-    _check(lib().fe_apply_host(ctx, ptr(X), ptr(Y), n_vec, _stream_ptr(stream)), "fe_apply_host")
+    n_vec = _host_blocks(ctx, X, Y)
+    _check(lib().fe_apply_host(ctx, _host_ptr(X), _host_ptr(Y), n_vec, _stream_ptr(stream)), "fe_apply_host")
 
 
-NOALLOC_STAGE_BYTES = 16 << 20
+def noalloc_stage_bytes() -> int:
+    """Size of the fixed device staging array of fe_apply_host_noalloc, as
+    compiled into the library."""
+    return int(lib().fe_noalloc_stage_bytes())
 
 
 def fe_apply_host_noalloc(ctx: int, X, Y, stream=None) -> None:
     """fe_apply_host without any device allocation by the library: the
-    staging lives in a fixed 16 MiB device array (for callers that cannot let
-    a library allocate device memory).  Overlapping calls race."""
-    import torch
-
-    def ptr(a):
-        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
-    _check(lib().fe_apply_host_noalloc(ctx, ptr(X), ptr(Y), X.shape[1], _stream_ptr(stream)), "fe_apply_host_noalloc")
+    staging lives in a fixed device array of noalloc_stage_bytes() (for
+    callers that cannot let a library allocate device memory).  Overlapping
+    calls race."""
+    n_vec = _host_blocks(ctx, X, Y)
+    _check(lib().fe_apply_host_noalloc(ctx, _host_ptr(X), _host_ptr(Y), n_vec, _stream_ptr(stream)),
+           "fe_apply_host_noalloc")
 
 
 def fe_diagonal(ctx: int, diag, stream=None) -> None:
