@@ -115,6 +115,22 @@ fe_status fe_precond_load(fe_ctx* ctx, const char* path);
 fe_status fe_mlp_gradients(fe_ctx* ctx, const float* U, const float* T, int rows, float* loss, float* gW1,
                            float* gb1, float* gW2, float* gb2, void* stream);
 
+/* Loss and gradients of the FE_TRAIN_ENERGY objective on one snapshot, as
+ * one training step computes them (the training kernels, exposed for
+ * checking).  R = r_k, Xk = x_k, Xstar = x* (device FP32, num_dofs x n_vec,
+ * DoF-major; r_k = A (x* - x_k) for a snapshot of a solve, though any blocks
+ * are accepted): every column is scaled by c_j = 1 / sqrt((x* - x_k)_j . r_j)
+ * (1 / ||r_j|| when that product is not positive), r' = c r, e' = c (x* - x_k),
+ * z = D^-1 r' + sum_e R_e^T (w_e .* s_e MLP(R_e r' / s_e)) with the current
+ * network, and
+ *   loss = (1 / n_vec) sum_j (z - e')_j^T A (z - e')_j
+ * with the FP32 operator.  Writes the loss to *loss (device) and dL/dW1,
+ * dL/db1, dL/dW2, dL/db2 to device buffers of the weight shapes (s_e depends
+ * on r alone, so it carries no gradient).  FE_EINVAL when no weights are set.
+ * Allocates its workspace for the call.  Synchronous. */
+fe_status fe_energy_gradients(fe_ctx* ctx, const float* R, const float* Xk, const float* Xstar, int n_vec,
+                              float* loss, float* gW1, float* gb1, float* gW2, float* gb2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -33,15 +34,30 @@ def _nvcc() -> str:
     return n
 
 
-def _deps_mtime() -> float:
-    files = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        glob.glob(os.path.join(INCLUDE, "*.h"))
-    return max(os.path.getmtime(f) for f in files) if files else 0.0
+_INC = re.compile(r'^\s*#\s*include\s*"([^"]+)"', re.M)
+
+
+def _local_deps(path: str, seen: set) -> set:
+    """Every quoted #include reachable from `path` that resolves to a file in
+    csrc/ or include/ (the only headers this library owns)."""
+    try:
+        text = open(path, encoding="utf-8", errors="replace").read()
+    except OSError:
+        return seen
+    for name in _INC.findall(text):
+        for base in (os.path.dirname(path), CSRC, INCLUDE):
+            cand = os.path.normpath(os.path.join(base, name))
+            if os.path.exists(cand):
+                if cand not in seen:
+                    seen.add(cand)
+                    _local_deps(cand, seen)
+                break
+    return seen
 
 
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(OBJS, os.path.basename(src)[:-3] + ".o")
-    newest = max(os.path.getmtime(src), _deps_mtime())
+    newest = max([os.path.getmtime(src)] + [os.path.getmtime(d) for d in _local_deps(src, set())])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj
     cmd = [_nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]

@@ -995,11 +995,96 @@ static void copy_weights(LearnedPrecond* L, float* W1, float* b1, float* W2, flo
   cp(b2, L->b2, L->n3);
 }
 
-// Train by the operator residual: over residual snapshots r (columns scaled to
-// norm 1), minimise mean (A z(r) - r)^2 with z the preconditioner output.
-// The gradient with respect to z is (2/N) A (A z - r) (A symmetric); it is
-// pulled back through the assembly to every patch output and then through the
-// network.  Two FP32 operator applications per step.
+// Buffers of the operator-in-the-loop objectives for one snapshot of nv columns.
+struct OpBufs {
+  float *U = nullptr, *S = nullptr, *rn = nullptr, *z = nullptr, *q = nullptr, *g = nullptr, *en = nullptr,
+        *cs = nullptr;
+};
+
+static cudaError_t alloc_op(OpBufs& o, size_t rows, int n3, size_t tot, int nv) {
+  cudaError_t e = cudaMalloc(&o.U, rows * n3 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&o.S, rows * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&o.cs, nv * sizeof(float));
+  for (float** p : {&o.rn, &o.z, &o.q, &o.g, &o.en})
+    if (e == cudaSuccess) e = cudaMalloc(p, tot * sizeof(float));
+  return e;
+}
+
+static void free_op(OpBufs& o) {
+  for (float* p : {o.U, o.S, o.rn, o.z, o.q, o.g, o.en, o.cs}) cudaFree(p);
+  o = OpBufs{};
+}
+
+// Loss and gradients of an operator-in-the-loop objective on one snapshot
+// (r = r_k, xk = x_k, xstar = x*; device FP32, num_dofs x nv), for the network
+// in L and all cells' patches at once (cells: device list of every cell):
+//  energy:   columns scaled by 1 / ||x* - x_k||_A = 1 / sqrt((x* - x_k) . r_k),
+//            loss = (1/nv) sum_j (z - e)_j^T A (z - e)_j, dL/dz = (2/nv) A (z - e)
+//            (one FP32 operator application);
+//  residual: columns scaled by 1 / ||r_k||, loss = (1/nv) ||A z - r||_F^2,
+//            dL/dz = (2/nv) A (A z - r) (two applications; A symmetric).
+// dL/dz is pulled back through the assembly (s_e w_i per patch entry; s_e is a
+// function of the input alone) and then through the network.  Leaves the loss
+// in tb.loss and the gradients in tb.gW1, tb.gb1, tb.gW2, tb.gb2.
+static fe_status operator_step(fe_ctx* c, bool energy, TrainBufs& tb, OpBufs& o, const int* cells, int nv,
+                               const float* r, const float* xk, const float* xstar, cudaStream_t s) {
+  LearnedPrecond* L = c->learned;
+  const int n3 = L->n3;
+  const size_t n = c->n_dofs, tot = n * nv;
+  const size_t rows = c->n_cells * (size_t)nv;
+  cudaError_t e;
+  if (energy) col_inv_energy_kernel<<<nv, 256, 0, s>>>(xstar, xk, r, o.cs, n, nv);
+  else col_invnorm_kernel<<<nv, 256, 0, s>>>(r, o.cs, n, nv);
+  col_scale_kernel<<<grid_for(tot), 256, 0, s>>>(r, nullptr, o.cs, o.rn, tot, nv);
+  if (energy) col_scale_kernel<<<grid_for(tot), 256, 0, s>>>(xk, xstar, o.cs, o.en, tot, nv);
+  gather_inputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, o.rn, nv, o.U, o.S);
+  if ((e = gemm((int)rows, kHidden, n3, o.U, n3, 1, L->W1, 1, n3, tb.Hpre, s)) != cudaSuccess) return from_cuda(e);
+  bias_act_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.Hpre, L->b1, (int)rows, kHidden, 1);
+  if ((e = gemm((int)rows, n3, kHidden, tb.Hpre, kHidden, 1, L->W2, 1, kHidden, tb.Y, s)) != cudaSuccess)
+    return from_cuda(e);
+  bias_act_kernel<<<grid_for(rows * n3), 256, 0, s>>>(tb.Y, L->b2, (int)rows, n3, 0);
+  jacobi_init_kernel<<<grid_for(tot), 256, 0, s>>>(o.rn, c->ws.dinv32, o.z, n, nv);
+  scatter_outputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, tb.Y, o.S, o.z, nv);
+  const fe_mode saved = c->mode;
+  c->mode = FE_FP32;
+  fe_status st;
+  if (energy) {
+    // loss = sum over columns of (z - e)^T A (z - e), divided by the number of
+    // columns (an O(1) value per column at any mesh size, which keeps the
+    // gradients well above Adam's epsilon); dL/dz = 2 A (z - e) / n_col
+    sub_kernel<<<grid_for(tot), 256, 0, s>>>(o.z, o.en, o.g, tot);
+    st = fe_apply(c, o.g, o.q, nv, s);
+    if (st == FE_OK) {
+      energy_loss_kernel<<<512, 256, 0, s>>>(o.g, o.q, o.rn, tot, 2.0f / (float)nv, tb.partial);
+      sum_kernel<<<1, 32, 0, s>>>(tb.partial, 512, 1.0f / (float)nv, tb.loss);
+      std::swap(o.q, o.rn);   // the gradient dL/dz now sits in q (rn is rebuilt next step)
+    }
+  } else {
+    st = fe_apply(c, o.z, o.q, nv, s);
+    if (st == FE_OK) {
+      residual_loss_kernel<<<512, 256, 0, s>>>(o.q, o.rn, o.g, tot, 2.0f / (float)nv, tb.partial);
+      sum_kernel<<<1, 32, 0, s>>>(tb.partial, 512, 1.0f / (float)nv, tb.loss);
+      st = fe_apply(c, o.g, o.q, nv, s);   // q <- A g = dL/dz
+    }
+  }
+  c->mode = saved;
+  if (st != FE_OK) return st;
+  gather_grad_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, o.q, o.S, tb.dY, nv);
+  if ((e = gemm(n3, kHidden, (int)rows, tb.dY, 1, n3, tb.Hpre, kHidden, 1, tb.gW2, s)) != cudaSuccess)
+    return from_cuda(e);
+  colsum_kernel<<<(n3 + 127) / 128, 128, 0, s>>>(tb.dY, (int)rows, n3, tb.gb2);
+  if ((e = gemm((int)rows, kHidden, n3, tb.dY, n3, 1, L->W2, kHidden, 1, tb.dH, s)) != cudaSuccess)
+    return from_cuda(e);
+  relu_grad_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.dH, tb.Hpre, rows * kHidden);
+  if ((e = gemm(kHidden, n3, (int)rows, tb.dH, 1, kHidden, o.U, n3, 1, tb.gW1, s)) != cudaSuccess)
+    return from_cuda(e);
+  colsum_kernel<<<1, 128, 0, s>>>(tb.dH, (int)rows, kHidden, tb.gb1);
+  return from_cuda(cudaGetLastError());
+}
+
+// Train by an operator-in-the-loop objective (operator_step) over the
+// recorded snapshots, one snapshot per Adam step, with the validation-based
+// checkpoint choice described in fe_learn.h.
 static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder& rec, const int* cells, int nv,
                                      fe_train_info* inf, cudaStream_t s, const float* xstar, Validation& val) {
   const bool energy = d->objective == FE_TRAIN_ENERGY;
@@ -1008,16 +1093,10 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
   const size_t n = c->n_dofs, tot = n * nv;
   const size_t rows = c->n_cells * (size_t)nv;
   TrainBufs tb;
-  float *U = nullptr, *S = nullptr, *rn = nullptr, *z = nullptr, *q = nullptr, *g = nullptr, *en = nullptr,
-        *cs = nullptr;
+  OpBufs ob;
   cudaError_t e = alloc_train(tb, (int)rows, n3);
-  if (e == cudaSuccess) e = cudaMalloc(&U, rows * n3 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&S, rows * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&cs, nv * sizeof(float));
-  for (float** p : {&rn, &z, &q, &g, &en})
-    if (e == cudaSuccess) e = cudaMalloc(p, tot * sizeof(float));
+  if (e == cudaSuccess) e = alloc_op(ob, rows, n3, tot, nv);
   fe_status st = from_cuda(e);
-  const fe_mode saved = c->mode;
   std::mt19937_64 rng(d->seed + 29);
   // checkpoints: epoch 0 is the network with a zero output layer (exactly Jacobi)
   Checkpoint best;
@@ -1047,49 +1126,8 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
     float ep_loss = 0.f;
     for (int oi = 0; oi < per_epoch && st == FE_OK; ++oi) {
       const int k = order[oi];
-      // r_k and e_k = x* - x_k scaled per column: by 1 / ||e_k||_A for the
-      // energy objective (every snapshot then weighs the same relative error),
-      // by 1 / ||r_k|| for the residual objective
-      if (energy) col_inv_energy_kernel<<<nv, 256, 0, s>>>(xstar, rec.x[k], rec.r[k], cs, n, nv);
-      else col_invnorm_kernel<<<nv, 256, 0, s>>>(rec.r[k], cs, n, nv);
-      col_scale_kernel<<<grid_for(tot), 256, 0, s>>>(rec.r[k], nullptr, cs, rn, tot, nv);
-      if (energy) col_scale_kernel<<<grid_for(tot), 256, 0, s>>>(rec.x[k], xstar, cs, en, tot, nv);
-      gather_inputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, rn, nv, U, S);
-      if ((e = gemm((int)rows, kHidden, n3, U, n3, 1, L->W1, 1, n3, tb.Hpre, s)) != cudaSuccess) break;
-      bias_act_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.Hpre, L->b1, (int)rows, kHidden, 1);
-      if ((e = gemm((int)rows, n3, kHidden, tb.Hpre, kHidden, 1, L->W2, 1, kHidden, tb.Y, s)) != cudaSuccess) break;
-      bias_act_kernel<<<grid_for(rows * n3), 256, 0, s>>>(tb.Y, L->b2, (int)rows, n3, 0);
-      jacobi_init_kernel<<<grid_for(tot), 256, 0, s>>>(rn, c->ws.dinv32, z, n, nv);
-      scatter_outputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, tb.Y, S, z, nv);
-      c->mode = FE_FP32;
-      if (energy) {
-        // loss = sum over columns of (z - e)^T A (z - e), divided by the number of
-        // columns (an O(1) value per column at any mesh size, which keeps the
-        // gradients well above Adam's epsilon); dL/dz = 2 A (z - e) / n_col
-        sub_kernel<<<grid_for(tot), 256, 0, s>>>(z, en, g, tot);
-        st = fe_apply(c, g, q, nv, s);
-        if (st == FE_OK) {
-          energy_loss_kernel<<<512, 256, 0, s>>>(g, q, rn, tot, 2.0f / (float)nv, tb.partial);
-          sum_kernel<<<1, 32, 0, s>>>(tb.partial, 512, 1.0f / (float)nv, tb.loss);
-          std::swap(q, rn);   // the gradient dL/dz now sits in q (rn is rebuilt next step)
-        }
-      } else {
-        st = fe_apply(c, z, q, nv, s);
-        if (st == FE_OK) {
-          residual_loss_kernel<<<512, 256, 0, s>>>(q, rn, g, tot, 2.0f / (float)nv, tb.partial);
-          sum_kernel<<<1, 32, 0, s>>>(tb.partial, 512, 1.0f / (float)nv, tb.loss);
-          st = fe_apply(c, g, q, nv, s);   // q <- A g = dL/dz
-        }
-      }
-      c->mode = saved;
+      st = operator_step(c, energy, tb, ob, cells, nv, rec.r[k], rec.x[k], xstar, s);
       if (st != FE_OK) break;
-      gather_grad_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, q, S, tb.dY, nv);
-      if ((e = gemm(n3, kHidden, (int)rows, tb.dY, 1, n3, tb.Hpre, kHidden, 1, tb.gW2, s)) != cudaSuccess) break;
-      colsum_kernel<<<(n3 + 127) / 128, 128, 0, s>>>(tb.dY, (int)rows, n3, tb.gb2);
-      if ((e = gemm((int)rows, kHidden, n3, tb.dY, n3, 1, L->W2, kHidden, 1, tb.dH, s)) != cudaSuccess) break;
-      relu_grad_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.dH, tb.Hpre, rows * kHidden);
-      if ((e = gemm(kHidden, n3, (int)rows, tb.dH, 1, kHidden, U, n3, 1, tb.gW1, s)) != cudaSuccess) break;
-      colsum_kernel<<<1, 128, 0, s>>>(tb.dH, (int)rows, kHidden, tb.gb1);
       adam_step(L, tb, d->lr, s);
       float h = 0.f;
       cudaMemcpyAsync(&h, tb.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -1111,7 +1149,6 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
       }
     }
   }
-  c->mode = saved;
   if (st == FE_OK && val.nv > 0) copy_weights(L, best.W1, best.b1, best.W2, best.b2, false, s);
   inf->val_jacobi_iterations = val_jac;
   inf->val_learned_iterations = best_its;
@@ -1123,10 +1160,49 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
   inf->steps = step;
   inf->samples = (long long)rows * rec.count;
   free_train(tb);
-  for (float* p : {U, S, rn, z, q, g, en, cs}) cudaFree(p);
+  free_op(ob);
   return st;
 }
 }  // namespace fe
+
+extern "C" fe_status fe_energy_gradients(fe_ctx* c, const float* R, const float* Xk, const float* Xstar, int n_vec,
+                                         float* loss, float* gW1, float* gb1, float* gW2, float* gb2, void* stream) {
+  if (!c || !c->learned || !R || !Xk || !Xstar || n_vec <= 0 || !loss || !gW1 || !gb1 || !gW2 || !gb2)
+    return FE_EINVAL;
+  if (c->refined) return FE_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LearnedPrecond* L = c->learned;
+  const int n3 = L->n3;
+  const size_t tot = c->n_dofs * (size_t)n_vec, rows = c->n_cells * (size_t)n_vec;
+  cudaError_t e = solver_workspace(c, n_vec);   // the Jacobi diagonal of z = D^-1 r + ...
+  if (e != cudaSuccess) return from_cuda(e);
+  std::vector<int> hcells(c->n_cells);
+  for (size_t k = 0; k < c->n_cells; ++k) hcells[k] = (int)k;
+  int* cells = nullptr;
+  TrainBufs tb;
+  OpBufs ob;
+  e = cudaMalloc(&cells, c->n_cells * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(cells, hcells.data(), c->n_cells * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = alloc_train(tb, (int)rows, n3);
+  if (e == cudaSuccess) e = alloc_op(ob, rows, n3, tot, n_vec);
+  fe_status st = from_cuda(e);
+  if (st == FE_OK) st = operator_step(c, true, tb, ob, cells, n_vec, R, Xk, Xstar, s);
+  const size_t w = (size_t)kHidden * n3;
+  if (st == FE_OK) {
+    e = cudaMemcpyAsync(loss, tb.loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(gW1, tb.gW1, w * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(gb1, tb.gb1, kHidden * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(gW2, tb.gW2, w * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(gb2, tb.gb2, n3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    st = from_cuda(e);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (st == FE_OK) st = from_cuda(e2);
+  free_train(tb);
+  free_op(ob);
+  cudaFree(cells);
+  return st;
+}
 
 extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_train_info* info, void* stream) {
   if (!c || !d || d->n_rhs <= 0 || d->snapshots <= 0 || d->snapshot_every <= 0 || d->epochs < 0 || d->batch <= 0 ||

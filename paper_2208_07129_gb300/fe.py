@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
         "fe_precond_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
         "fe_precond_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
         "fe_mlp_gradients": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
+        "fe_energy_gradients": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
         "fe_mass_gll": (ctypes.c_int, [_VP, _DP]),
         "fe_setup_refined": (ctypes.c_int, [ctypes.POINTER(fe_refined_desc), ctypes.c_int,
                                             ctypes.POINTER(fe_quad_desc), ctypes.c_double, ctypes.POINTER(_VP)]),
@@ -444,6 +445,25 @@ def fe_mlp_gradients(ctx: int, U, T, stream=None):
          torch.zeros(n3, device=dev)]
     _check(lib().fe_mlp_gradients(ctx, U.data_ptr(), T.data_ptr(), U.shape[0], loss.data_ptr(),
                                   *[x.data_ptr() for x in g], _stream_ptr(stream)), "fe_mlp_gradients")
+    return loss, g
+
+
+def fe_energy_gradients(ctx: int, R, Xk, Xstar, stream=None):
+    """Loss and gradients of the energy training objective on one snapshot
+    (r_k, x_k, x*: CUDA float32 blocks (num_dofs, n_vec)); torch tensors out."""
+    import torch
+    for t, nm in ((R, "R"), (Xk, "Xk"), (Xstar, "Xstar")):
+        if (not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.dim() != 2
+                or t.shape != R.shape or t.shape[0] != fe_num_dofs(ctx)):
+            raise ValueError(f"{nm}: need a contiguous CUDA float32 tensor of shape (num_dofs, n_vec)")
+    n3 = fe_precond_input_size(ctx)
+    dev = R.device
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    g = [torch.zeros(HIDDEN, n3, device=dev), torch.zeros(HIDDEN, device=dev), torch.zeros(n3, HIDDEN, device=dev),
+         torch.zeros(n3, device=dev)]
+    _check(lib().fe_energy_gradients(ctx, R.data_ptr(), Xk.data_ptr(), Xstar.data_ptr(), R.shape[1],
+                                     loss.data_ptr(), *[x.data_ptr() for x in g], _stream_ptr(stream)),
+           "fe_energy_gradients")
     return loss, g
 
 

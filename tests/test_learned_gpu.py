@@ -48,6 +48,42 @@ def test_gradients_match_oracle(fe):
         fe.fe_destroy(ctx)
 
 
+@pytest.mark.parametrize("p,nx,periodic", [(3, 2, False), (2, 3, True)])
+def test_energy_gradients_match_oracle(fe, p, nx, periodic):
+    """The objective training actually uses (energy norm of what the
+    preconditioner misses, operator in the loop, patch scale s_e, partition
+    weights) against the FP64 oracle, through the C ABI."""
+    nq = p + 2
+    ctx = fe.fe_setup(nx, nx, nx, p, nq, periodic=periodic)
+    mesh = orc.Mesh(nx, nx, nx, periodic=periodic)
+    try:
+        n, n3, nv = fe.fe_num_dofs(ctx), (p + 1) ** 3, 12
+        V = np.full(mesh.num_cells * nq ** 3, 0.7)
+        fe.fe_set_potential(ctx, V)
+        A = orc.assemble(mesh, p, nq, Vq=V)
+        W = _weights(n3, 10 + p)
+        fe.fe_precond_set_weights(ctx, *W)
+        rng = np.random.default_rng(p)
+        con = orc.constrained_mask(mesh, p)
+        xs, xk = rng.normal(size=(n, nv)), rng.normal(size=(n, nv))
+        xs[con] = 0.0
+        xk[con] = 0.0
+        xs, xk = xs.astype(np.float32), xk.astype(np.float32)
+        r = (A @ (xs.astype(np.float64) - xk)).astype(np.float32)
+        d = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_diagonal(ctx, d)
+        dinv = (1.0 / d.cpu().numpy()).astype(np.float32).astype(np.float64)
+        loss, g = fe.fe_energy_gradients(ctx, *[torch.from_numpy(a).cuda() for a in (r, xk, xs)])
+        ref = mo.energy_loss_and_grads(mesh, p, A, dinv, *[w.astype(np.float64) for w in W],
+                                       r.astype(np.float64), xk.astype(np.float64), xs.astype(np.float64))
+        assert abs(loss.item() - ref[0]) <= 1e-4 * ref[0], (loss.item(), ref[0])
+        for got, want in zip(g, ref[1:]):
+            got = got.cpu().numpy()
+            assert np.linalg.norm(got - want) <= 1e-4 * np.linalg.norm(want)
+    finally:
+        fe.fe_destroy(ctx)
+
+
 @pytest.mark.parametrize("p,nv,periodic", [(3, 128, False), (6, 130, False), (4, 40, True)])
 def test_inference_matches_oracle(fe, p, nv, periodic):
     nx = 3 if p < 6 else 2
@@ -124,22 +160,34 @@ def test_training_gain_over_jacobi(fe):
 
 
 def test_checkpoint_never_worse_than_jacobi(fe):
-    """With no useful epoch (zero learning rate is not allowed, so one tiny
-    epoch), the kept checkpoint falls back to the zero output layer and the
-    learned solve takes exactly the Jacobi iterations."""
+    """The kept checkpoint is never worse than Jacobi on the held-out
+    right-hand sides.  With no training epoch the only candidate is epoch 0,
+    the network with a zero output layer, which is exactly Jacobi: the kept
+    weights must have W2 = b2 = 0 and the learned solve must converge like
+    Jacobi (the same preconditioner; the flexible-CG coefficient only changes
+    the rounding).  After one real epoch the validation count may not exceed
+    Jacobi's either."""
     w = inputs.Workload("4^3 p=4", 4, 4, 4, False, 4, 6, 8, "normal", 78, "gauss", v_seed=15, v_amp=0.125,
                         v_shift=1.0)
     ctx = fe.setup_workload(w)
     try:
-        info = fe.fe_precond_train(ctx, n_rhs=8, snapshots=2, snapshot_every=5, epochs=1, batch=256, lr=1e-9,
+        fe.fe_precond_init(ctx, seed=9)
+        info = fe.fe_precond_train(ctx, n_rhs=8, snapshots=2, snapshot_every=5, epochs=0, batch=256, lr=1e-3,
                                    traj_rtol=1e-6, seed=5, objective="energy", n_val=4)
-        assert info["val_learned_iterations"] <= info["val_jacobi_iterations"]
+        assert info["best_epoch"] == 0
+        assert info["val_learned_iterations"] == info["val_jacobi_iterations"]
+        W1, b1, W2, b2 = fe.fe_precond_get_weights(ctx)
+        assert not np.any(W2) and not np.any(b2)
         B = torch.from_numpy(w.make_rhs(8)).cuda()
         its = {}
         for pc in ("jacobi", "learned"):
             X = torch.zeros_like(B)
-            its[pc] = fe.fe_solve(ctx, B, X, rtol=1e-8, max_it=20000, precond=pc, inner_mode="fp32")["iterations"]
-        if info["best_epoch"] == 0:
-            assert its["learned"] == its["jacobi"], its
+            r = fe.fe_solve(ctx, B, X, rtol=1e-8, max_it=20000, precond=pc, inner_mode="fp32")
+            assert r["status"] == fe.FE_OK and r["max_rel_residual"] <= 1e-8
+            its[pc] = r["iterations"]
+        assert abs(its["learned"] - its["jacobi"]) <= max(2, its["jacobi"] // 50), its
+        info = fe.fe_precond_train(ctx, n_rhs=8, snapshots=2, snapshot_every=5, epochs=1, batch=256, lr=1e-9,
+                                   traj_rtol=1e-6, seed=5, objective="energy", n_val=4)
+        assert info["val_learned_iterations"] <= info["val_jacobi_iterations"]
     finally:
         fe.fe_destroy(ctx)
