@@ -62,11 +62,12 @@ def flops_per_cell_vec(np_: int, nq: int) -> int:
     return 4 * (np_ ** 3 * nq + np_ ** 2 * nq ** 2 + np_ * nq ** 3) + 12 * nq ** 4 + 16 * nq ** 3
 
 
-def bytes_per_apply(w, elem: int) -> int:
-    """Algorithmic HBM bytes: X read once, Y written once, V coefficient per point
-    (8 B), and per-point metric (6 values) on trilinear meshes."""
+def bytes_per_apply(w, elem: int, geo_elem: int = 0) -> int:
+    """Algorithmic HBM bytes: X read once, Y written once (elem bytes each), the
+    V coefficient per point and the per-point metric (6 values) on trilinear
+    meshes (geo_elem bytes each; default elem)."""
     nq3 = w.nq ** 3
-    geo = w.num_cells * nq3 * elem * (7 if w.perturb_seed is not None else 1)
+    geo = w.num_cells * nq3 * (geo_elem or elem) * (7 if w.perturb_seed is not None else 1)
     return w.num_dofs * w.n_vec * 2 * elem + geo
 
 
@@ -185,83 +186,121 @@ FP64_KERNEL = "cell_apply_eo_kernel<double,7,8,false>"
 
 
 class OracleSample:
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
-    the workload: rows of A X, each row assembled from its cell matrices by
-    FP64 quadrature and multiplied with the vector block."""
+    """The FP64 oracle as it stands, on the host cores, on a bounded block of
+    the workload: a contiguous block of rows of A (from the middle of the
+    mesh) is assembled once into CSR by the oracle (its own quadrature, cell
+    matrix rows and merge; timed and reported as assembly_s, not part of the
+    rate), then every timed run is the oracle's OpenMP CSR x block product
+    over that block with the workload's n_vec columns."""
 
-    def __init__(self, w):
+    MAX_ROWS = 16384
+
+    def __init__(self, w, assembly_budget_s: float = 6.0):
         from oracle import oracle as orc
         self.orc, self.w = orc, w
         self.mesh = orc.Mesh(w.nx, w.ny, w.nz, periodic=w.periodic, vertices=w.vertices())
         self.Vo = w.potential_at(orc.quad_points(self.mesh, w.p, w.nq))
         self.X = inputs.random_block(w.num_dofs, w.n_vec, w.x_dist, w.x_seed)
-        self.rng = np.random.default_rng(0)
-        self.rows_per_s = None
-
-    def run(self, n_rows: int) -> float:
-        rows = np.sort(self.rng.integers(0, self.w.num_dofs, n_rows))
+        # size the block by the assembly rate of a small probe
+        probe = 8 * orc.num_threads()
         t0 = time.perf_counter()
-        self.orc.apply_rows(self.mesh, self.w.p, self.w.nq, self.X, rows, Vq=self.Vo, mu=self.w.mu)
-        dt = time.perf_counter() - t0
-        self.rows_per_s = n_rows / dt
+        self._assemble(probe)
+        rate = probe / max(time.perf_counter() - t0, 1e-6)
+        n = int(min(self.MAX_ROWS, w.num_dofs, max(probe, rate * assembly_budget_s)))
+        t0 = time.perf_counter()
+        self._assemble(n)
+        self.assembly_s = time.perf_counter() - t0
+        self.n_rows = n
+        self.nnz = int(self.B.nnz)
+        self.spmm_s = None
+
+    def _assemble(self, n: int):
+        r0 = max(0, min(self.w.num_dofs - n, self.w.num_dofs // 2))
+        self.r0 = r0
+        self.B = self.orc.assemble_rows(self.mesh, self.w.p, self.w.nq, np.arange(r0, r0 + n), Vq=self.Vo,
+                                        mu=self.w.mu)
+
+    def run(self, reps: int = 1) -> float:
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            self.orc.spmm(self.B, self.X)
+        dt = (time.perf_counter() - t0) / reps
+        self.spmm_s = dt
         return dt
 
     def sized(self, budget_s: float) -> int:
-        if self.rows_per_s is None:
-            self.run(8 * self.orc.num_threads())
-        return max(8, int(self.rows_per_s * budget_s))
+        """Products per timed run so that one run takes about budget_s."""
+        if self.spmm_s is None:
+            self.run(1)
+        return max(1, int(budget_s / max(self.spmm_s, 1e-6)))
 
-    def result(self, n_rows: int, dt: float) -> dict:
+    def seconds_per_apply(self) -> float:
+        return self.spmm_s / self.n_rows * self.w.num_dofs
+
+    def result(self, reps: int, dt: float) -> dict:
         w = self.w
-        return {"value": n_rows * w.n_vec / dt / 1e9, "unit": UNIT, "cores": self.orc.num_threads(), "kind": "oracle",
-                "sample": f"{n_rows} of {w.num_dofs} rows of A X ({w.name}), each row assembled from its cell "
-                          f"matrices by FP64 quadrature and multiplied with the {w.n_vec}-vector block; {dt:.1f} s"}
+        return {"value": self.n_rows * w.n_vec / dt / 1e9, "unit": UNIT, "cores": self.orc.num_threads(),
+                "kind": "oracle", "assembly_s": self.assembly_s, "rows": self.n_rows, "nnz": self.nnz,
+                "sample": f"rows {self.r0}..{self.r0 + self.n_rows - 1} of {w.num_dofs} of A ({w.name}; "
+                          f"{self.nnz} nonzeros) assembled once into CSR by the oracle in {self.assembly_s:.1f} s "
+                          f"(not timed), then the oracle's OpenMP CSR x {w.n_vec}-vector block product over that "
+                          f"block, {reps} products, {dt * 1e3:.1f} ms each"}
 
 
-def cpu_baseline(w, budget_s: float = 12.0):
+def cpu_baseline(w, budget_s: float = 8.0):
     o = OracleSample(w)
-    n = o.sized(budget_s)
-    return o.result(n, o.run(n))
+    reps = o.sized(budget_s)
+    return o.result(reps, o.run(reps))
 
 
-def cpu_pcg_extrapolated(w, iterations: int, budget_s: float = 8.0) -> dict:
+def cpu_pcg_extrapolated(w, iterations: int, budget_s: float = 4.0) -> dict:
     """The oracle's time to solution for Jacobi-PCG on `w`, extrapolated: one
-    full oracle apply (rate measured on a bounded sample of rows) times the
-    FP64 iteration count of the GPU solve.  Vector updates and reductions are
-    not counted, so the figure is a lower bound."""
+    full oracle apply (the CSR x block rate measured on an assembled row block,
+    scaled to all rows) times the FP64 iteration count of the GPU solve.
+    Assembly, vector updates and reductions are not counted, so the figure is
+    a lower bound."""
     o = OracleSample(w)
-    n = o.sized(budget_s)
-    dt = o.run(n)
-    s_apply = dt / n * w.num_dofs
+    reps = o.sized(budget_s)
+    dt = o.run(reps)
+    s_apply = o.seconds_per_apply()
     return {"kind": "oracle", "cores": o.orc.num_threads(), "extrapolated": True,
             "seconds_per_apply": s_apply, "iterations": iterations, "seconds_extrapolated": s_apply * iterations,
-            "sample": f"{n} of {w.num_dofs} rows of A X with {w.n_vec} columns ({dt:.1f} s), scaled to all rows; "
-                      f"vector updates not counted"}
+            "assembly_s_block": o.assembly_s,
+            "sample": f"CSR x {w.n_vec}-column product over {o.n_rows} assembled rows of {w.num_dofs} "
+                      f"({reps} products, {dt * 1e3:.1f} ms each), scaled to all rows; assembly and vector "
+                      f"updates not counted"}
+
+
+def bench_config(w) -> dict:
+    """The `config` object of both arms' JSON lines (same keys)."""
+    return {"workload": w.name, "dofs": w.num_dofs, "cells": w.num_cells, "p": w.p, "n_q": w.nq,
+            "n_vec": w.n_vec, "l2": "inputs larger than L2 (3.6 GB per FP64 block), no flush"}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores (rank 0 only); each
-    step is a bounded sample of rows of the 32^3 workload."""
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only).  Its
+    row block is assembled once before the warm-up; each step is the oracle's
+    CSR x block product over that block of the 32^3 workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = inputs.WORKLOADS["c2"]
     o = OracleSample(w)
-    n = o.sized(max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+    reps = o.sized(max(1.0, 40.0 / max(1, args.warmup + args.steps)))
     for _ in range(args.warmup):
-        o.run(n)
+        o.run(reps)
     vals, dts = [], []
     for _ in range(args.steps):
-        dt = o.run(n)
+        dt = o.run(reps)
         dts.append(dt)
-        vals.append(n * w.n_vec / dt / 1e9)
+        vals.append(o.n_rows * w.n_vec / dt / 1e9)
     v = statistics.median(vals)
-    cb = o.result(n, statistics.median(dts))
+    cb = o.result(reps, statistics.median(dts))
     cb["value"] = v
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(dts) * 1e3,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": w.name, "dofs": w.num_dofs, "n_vec": w.n_vec},
+                      "data": "synthetic", "config": bench_config(w),
                       "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                                   "d2h_bytes_per_step": 0}}), flush=True)
 
@@ -270,8 +309,7 @@ def time_mode(fe, torch, ctx, w, mode, steps, warmup, world):
     """Device-timed applies (CUDA events on the launching stream) and per-launch
     duration of the cell kernel; returns (ms_per_step, launches_per_step)."""
     fe.fe_set_mode(ctx, mode)
-    dt = torch.float64 if mode in ("fp64", "df64") else torch.float32
-    X = torch.from_numpy(w.make_x()).to(device="cuda", dtype=dt)
+    X = torch.from_numpy(w.make_x()).to(device="cuda", dtype=fe.block_dtype(ctx))
     Y = torch.empty_like(X)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -679,7 +717,7 @@ def main():
 
     modes = {}
     want = args.modes.split(",")
-    extra_modes = [m for m in ("df64", "tf32", "bf16", "tf32x3") if m in want or args.modes == "fp64,fp32"]
+    extra_modes = [m for m in ("df64", "tf32", "bf16", "bf16s", "tf32x3") if m in want or args.modes == "fp64,fp32"]
     with ClockSampler(local) as clk:
         ms64 = ms32 = float("nan")
         X64 = Y64 = X32 = Y32 = None
@@ -762,19 +800,25 @@ def main():
                         "speedup_vs_fp64": ms64 / ms_tc[m],
                         "hbm_frac": b64 / (ms_tc[m] * 1e-3) / 1e9 / hbm}
             continue
+        io = 2 if m == "bf16s" else 4
+        bt = bytes_per_apply(w, io, 4)
+        gbs = bt / (ms_tc[m] * 1e-3) / 1e9
         modes[m] = {"value": total_units / (ms_tc[m] * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_tc[m],
-                    "dtype": "f32 data, %s tensor-core contractions, f32 accumulation"
-                             % ("split-TF32 (hi+lo, 3 products)" if m == "tf32x3" else m),
+                    "dtype": ("bf16 data, bf16 tensor-core contractions, f32 accumulation" if m == "bf16s" else
+                              "f32 data, %s tensor-core contractions, f32 accumulation"
+                              % ("split-TF32 (hi+lo, 3 products)" if m == "tf32x3" else m)),
                     "rel_err_vs_oracle": acc.get(m), "algorithmic_tflops": ach,
-                    "hbm_frac": b32 / (ms_tc[m] * 1e-3) / 1e9 / hbm}
+                    "kernel": "tc_apply_kernel (tcgen05)" if m != "tf32x3" else "mma_apply_kernel (warp MMA)",
+                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                 "algorithmic_bytes": bt},
+                    "hbm_frac": gbs / hbm}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms64, "ms_per_step_median": statistics.median(per64),
         "ms_per_step_min": min(per64), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "dofs": w.num_dofs, "cells": w.num_cells, "p": w.p, "n_q": w.nq,
-                   "n_vec": w.n_vec, "l2": "inputs larger than L2 (3.6 GB per FP64 block), no flush",
-                   "rel_err_vs_oracle": acc.get("fp64"), "sampled_rows": 48},
+        "config": bench_config(w),
+        "rel_err_vs_oracle": acc.get("fp64"), "sampled_rows": 48,
         "roofline": {"bound": "alu", "achieved": ach64, "peak": pk64, "unit": "TFLOP/s", "frac": ach64 / pk64,
                      "traffic": traffic, "hbm_frac": b64 / (ms64 * 1e-3) / 1e9 / hbm,
                      "kernel": FP64_KERNEL,

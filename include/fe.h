@@ -16,7 +16,8 @@
  *  - Multivectors are DoF-major and vector-contiguous (the paper's batched
  *    contiguous layout, Sec. 3.2.1, with one batch holding all n_vec
  *    vectors): element (dof, v) lives at X[dof * n_vec + v].  The dtype is
- *    double in FE_FP64 mode and float in every other mode.
+ *    double in FE_FP64 and FE_DF64 modes, bfloat16 in FE_BF16S mode and float
+ *    in every other mode.
  *  - Global node (gx, gy, gz) has index gx + Nx (gy + Ny gz), where Nx = nx p + 1
  *    for a Dirichlet box and Nx = nx p for a periodic box (wrap-around).
  *  - Cells are e = cx + nx (cy + ny cz); quadrature points Q = q1 + n_q (q2 + n_q q3).
@@ -68,9 +69,14 @@ typedef enum { FE_QUAD_GAUSS = 0, FE_QUAD_GLL = 1 } fe_quad_kind;
  * value an unevaluated sum of two floats, ~48 significant bits; error-free
  * sums and products, compensated dot products) on the FP32 pipe, which
  * GB300 runs at 64 times its FP64 rate; errors stay within the FP64 bound
- * (1e-12 relative).
+ * (1e-12 relative).  FE_BF16S: as FE_BF16, but X and Y are bfloat16 in
+ * device memory (half the bytes of FE_BF16); the colour-ordered accumulation
+ * of Y rounds to bfloat16 after every add.  FE_TF32, FE_BF16 and FE_BF16S run
+ * on the tcgen05 tensor cores (operands in shared memory, FP32 accumulators in
+ * tensor memory) when n_p <= 8 and n_q <= 8; FE_TF32 and FE_BF16 fall back to
+ * warp-level MMA kernels otherwise, FE_BF16S is then FE_EUNSUPPORTED.
  * Geometry is always computed in FP64. */
-typedef enum { FE_FP64 = 0, FE_FP32 = 1, FE_TF32 = 2, FE_BF16 = 3, FE_TF32X3 = 4, FE_DF64 = 5 } fe_mode;
+typedef enum { FE_FP64 = 0, FE_FP32 = 1, FE_TF32 = 2, FE_BF16 = 3, FE_TF32X3 = 4, FE_DF64 = 5, FE_BF16S = 6 } fe_mode;
 
 typedef struct {
   int nx, ny, nz;          /* cells per direction, >= 1 (>= 2 when periodic) */
@@ -177,8 +183,10 @@ fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream)
  * kernel; FE_FP32: 0 or 1 = line kernel, 2 = register-plane kernel, n_q <= 8
  * only, 3 = line kernel with even-odd contractions; FE_DF64: 0, the
  * double-float even-odd line kernel).
- * FE_EUNSUPPORTED for the tensor-core modes, whose tile is fixed.  Applies to
- * later fe_apply calls. */
+ * FE_TF32 / FE_BF16: the tile is fixed; variant 0 = tcgen05 kernel where
+ * built (n_p, n_q <= 8), 1 = warp-level MMA kernel (the other arguments are
+ * ignored).  FE_TF32X3 and FE_BF16S: FE_EUNSUPPORTED.  Applies to later
+ * fe_apply calls. */
 fe_status fe_set_tile(fe_ctx* ctx, fe_mode mode, int vectors_per_cta, int lines, int variant);
 
 /* Same product with HOST buffers (num_dofs x n_vec, DoF-major, in the

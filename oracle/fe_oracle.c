@@ -573,6 +573,80 @@ int oracle_assemble_csr(const oracle_mesh* m, int p, int nq, int quad_kind, doub
   return status;
 }
 
+/* Rows rows[0..n_rows) of the global CSR matrix, assembled without forming
+ * whole cell matrices: each row sums, over its incident cells, the one
+ * matching row of the cell matrix (the same quadrature sums and the same
+ * merge as oracle_assemble_csr, restricted to the requested rows).  Two calls
+ * as for oracle_assemble_csr: first with col == NULL for rowptr (n_rows + 1
+ * entries), then with col/val sized rowptr[n_rows].  Used to time the CSR x
+ * block product on a bounded row block of a mesh too large to assemble. */
+int oracle_assemble_rows_csr(const oracle_mesh* m, int p, int nq, int quad_kind, double mu, const double* Vq,
+                             int constrain, const long* rows, long n_rows, long* rowptr, long* col, double* val) {
+  if (!mesh_ok(m, p)) return OR_EINVAL;
+  ref1d r;
+  if (make_ref1d(p, nq, quad_kind, &r) != OR_OK) return OR_EINVAL;
+  long n = oracle_num_dofs(m, p);
+  long np3 = (long)r.np * r.np * r.np, nq3 = (long)nq * nq * nq;
+  int status = OR_OK;
+#pragma omp parallel
+  {
+    cell_points cp;
+    int ok = alloc_points(&r, &cp) == OR_OK;
+    double* rowbuf = (double*)malloc(sizeof(double) * np3);
+    long* gdofs = (long*)malloc(sizeof(long) * np3);
+    long* cols = (long*)malloc(sizeof(long) * 8 * np3);
+    double* vals = (double*)malloc(sizeof(double) * 8 * np3);
+    long* pos = (long*)malloc(sizeof(long) * n);
+    long cells[8];
+    int locals[8];
+    if (!ok || !rowbuf || !gdofs || !cols || !vals || !pos) {
+#pragma omp critical
+      status = OR_ENOMEM;
+    } else {
+      for (long I = 0; I < n; ++I) pos[I] = -1;
+#pragma omp for schedule(dynamic, 1)
+      for (long k = 0; k < n_rows; ++k) {
+        long I = rows[k], cnt = 0;
+        if (I < 0 || I >= n) {
+#pragma omp critical
+          status = OR_EINVAL;
+          continue;
+        }
+        if (!(constrain && oracle_is_constrained(m, p, I))) {
+          int nc = incident_cells(m, p, I, cells, locals);
+          for (int c = 0; c < nc; ++c) {
+            if (cell_point_data(m, &r, cells[c], mu, Vq ? Vq + cells[c] * nq3 : NULL, &cp) != OR_OK) {
+#pragma omp critical
+              status = OR_EGEOM;
+              break;
+            }
+            cell_matrix_rows(&r, &cp, locals[c], locals[c] + 1, rowbuf);
+            oracle_cell_dofs(m, p, cells[c], gdofs);
+            cnt = merge_row(m, p, constrain, gdofs, np3, rowbuf, cnt, cols, vals, pos);
+          }
+          for (long t = 0; t < cnt; ++t) pos[cols[t]] = -1;
+          sort_row(cnt, cols, vals);
+        }
+        if (col == NULL) {
+          rowptr[k + 1] = cnt;
+        } else {
+          for (long t = 0; t < cnt; ++t) {
+            col[rowptr[k] + t] = cols[t];
+            val[rowptr[k] + t] = vals[t];
+          }
+        }
+      }
+    }
+    if (ok) free_points(&cp);
+    free(rowbuf); free(gdofs); free(cols); free(vals); free(pos);
+  }
+  if (status == OR_OK && col == NULL) {
+    rowptr[0] = 0;
+    for (long k = 0; k < n_rows; ++k) rowptr[k + 1] += rowptr[k];
+  }
+  return status;
+}
+
 /* Y = A X for a CSR matrix and a DoF-major block X[dof * n_vec + v]. */
 int oracle_csr_spmm(long n_rows, const long* rowptr, const long* col, const double* val,
                     const double* X, int n_vec, double* Y) {

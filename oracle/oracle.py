@@ -75,6 +75,8 @@ def _L():
         _lib.oracle_assemble_csr.argtypes = [mp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              dp, ctypes.c_int, lp, lp, dp]
         _lib.oracle_csr_spmm.argtypes = [ctypes.c_long, lp, lp, dp, dp, ctypes.c_int, dp]
+        _lib.oracle_assemble_rows_csr.argtypes = [mp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                  dp, ctypes.c_int, lp, ctypes.c_long, lp, lp, dp]
         _lib.oracle_apply_rows.argtypes = [mp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            dp, ctypes.c_int, dp, ctypes.c_int, lp, ctypes.c_long, dp]
         _lib.oracle_num_threads.restype = ctypes.c_int
@@ -209,13 +211,35 @@ def assemble(mesh: Mesh, p: int, nq: int, kind: int = GAUSS, mu: float = 0.5,
     return sp.csr_matrix((val, col, rowptr), shape=(n, n))
 
 
+def assemble_rows(mesh: Mesh, p: int, nq: int, rows: np.ndarray, kind: int = GAUSS, mu: float = 0.5,
+                  Vq: Optional[np.ndarray] = None, constrain: bool = True):
+    """Rows ``rows`` of the global matrix as a CSR block (len(rows) x num_dofs),
+    each row assembled from the matching rows of its cells' matrices."""
+    import scipy.sparse as sp
+    n = num_dofs(mesh, p)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    Vq = None if Vq is None else np.ascontiguousarray(Vq, dtype=np.float64)
+    rowptr = np.zeros(len(rows) + 1, dtype=np.int64)
+    m = mesh.c()
+    lib = _L()
+    null_l = ctypes.POINTER(ctypes.c_long)()
+    _check(lib.oracle_assemble_rows_csr(ctypes.byref(m), p, nq, kind, mu, _dp(Vq), int(constrain), _lp(rows),
+                                        len(rows), _lp(rowptr), null_l, _dp(None)), "assemble_rows(count)")
+    nnz = int(rowptr[-1])
+    col = np.zeros(nnz, dtype=np.int64)
+    val = np.zeros(nnz)
+    _check(lib.oracle_assemble_rows_csr(ctypes.byref(m), p, nq, kind, mu, _dp(Vq), int(constrain), _lp(rows),
+                                        len(rows), _lp(rowptr), _lp(col), _dp(val)), "assemble_rows(fill)")
+    return sp.csr_matrix((val, col, rowptr), shape=(len(rows), n))
+
+
 def spmm(A, X: np.ndarray) -> np.ndarray:
     """Y = A X with the oracle's own OpenMP CSR x dense-block product."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     if X.ndim == 1:
         X = X[:, None]
-    n, nv = X.shape
-    Y = np.zeros_like(X)
+    nv = X.shape[1]
+    Y = np.zeros((A.shape[0], nv))
     rowptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
     col = np.ascontiguousarray(A.indices, dtype=np.int64)
     val = np.ascontiguousarray(A.data, dtype=np.float64)

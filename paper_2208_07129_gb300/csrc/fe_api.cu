@@ -9,7 +9,9 @@ namespace {
 fe_status from_cuda(cudaError_t e) {
   return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
 }
-size_t elem_size(fe_mode m) { return (m == FE_FP64 || m == FE_DF64) ? sizeof(double) : sizeof(float); }
+size_t elem_size(fe_mode m) {
+  return (m == FE_FP64 || m == FE_DF64) ? sizeof(double) : m == FE_BF16S ? (size_t)2 : sizeof(float);
+}
 
 bool overlaps(const void* a, const void* b, size_t bytes) {
   const char* x = static_cast<const char*>(a);
@@ -36,9 +38,18 @@ extern "C" fe_status fe_apply(fe_ctx* c, const void* X, void* Y, int n_vec, void
     case FE_FP32: e = apply_cc_f32(c, static_cast<const float*>(X), static_cast<float*>(Y), n_vec, s); break;
     case FE_TF32:
     case FE_BF16:
+      if (c->tc_variant == 0 && tc_supported(c)) {
+        e = apply_tc(c, X, Y, n_vec, s, c->mode);
+        break;
+      }
+      [[fallthrough]];
     case FE_TF32X3:
       if ((size_t)3 * c->nq * c->nq * c->nq * 16 * sizeof(float) > 220 * 1024) return FE_EUNSUPPORTED;
       e = apply_mma_f32(c, static_cast<const float*>(X), static_cast<float*>(Y), n_vec, s, c->mode);
+      break;
+    case FE_BF16S:
+      if (!tc_supported(c)) return FE_EUNSUPPORTED;
+      e = apply_tc(c, X, Y, n_vec, s, c->mode);
       break;
     default: return FE_EUNSUPPORTED;
   }

@@ -157,6 +157,10 @@ struct fe_ctx {
   int vb64 = 8, nty64 = 16, vb32 = 8, nty32 = 32, vbdf = 8, ntydf = 32;
   int fp32_variant = 0;   // 0 / 1: line kernel, 2: register-plane kernel, 3: even-odd line kernel
   int fp64_variant = 0;   // 0: even-odd line kernel, 1: plain line kernel
+  int tc_variant = 0;     // FE_TF32 / FE_BF16: 0 tcgen05 kernel (where built), 1 warp-MMA kernel
+  // B operands of the tcgen05 kernel's six passes (TF32, BF16), built at setup
+  // when n_p, n_q <= 8
+  unsigned char* d_tcimg[2] = {nullptr, nullptr};
 };
 
 namespace fe {
@@ -171,6 +175,10 @@ cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, c
 cudaError_t diagonal_f64(const fe_ctx* c, double* diag, cudaStream_t s);
 cudaError_t apply_mma_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s, fe_mode mode);
 cudaError_t apply_df64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s);
+// tcgen05 cell kernel (fe_apply_tc.cu): FE_TF32, FE_BF16 (FP32 data) and FE_BF16S (BF16 data).
+cudaError_t build_tc_images(fe_ctx* c);
+bool tc_supported(const fe_ctx* c);
+cudaError_t apply_tc(const fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s, fe_mode mode);
 cudaError_t apply_scaled_df64(const fe_ctx* c, const double* X, double* Y, int n_vec, const Scale<double>& sc,
                               cudaStream_t s);
 cudaError_t apply_scaled_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, const Scale<double>& sc,

@@ -57,7 +57,8 @@ extern "C" fe_status fe_apply_host_noalloc(fe_ctx* c, const void* Xh, void* Yh, 
   if (!Xh || !Yh) return FE_EINVAL;
   // refuse what fe_apply would refuse before any copy is queued
   if (c->refined && c->mode != FE_FP64 && c->mode != FE_DF64 && c->mode != FE_FP32) return FE_EUNSUPPORTED;
-  const size_t elem = (c->mode == FE_FP64 || c->mode == FE_DF64) ? sizeof(double) : sizeof(float);
+  const size_t elem =
+      (c->mode == FE_FP64 || c->mode == FE_DF64) ? sizeof(double) : c->mode == FE_BF16S ? (size_t)2 : sizeof(float);
   const size_t bytes = c->n_dofs * (size_t)n_vec * elem;
   // X, Y and (on a refined mesh with hanging nodes) the distribute step's copy
   // of X with the slave rows filled in, each block at a 256-byte boundary

@@ -379,6 +379,7 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
     std::vector<double> zero(E * nq3, 0.0);
     err = upload_point_coeff(c, zero);
   }
+  if (err == cudaSuccess) err = build_tc_images(c);
   if (err != cudaSuccess) { fe_destroy(c); return from_cuda(err); }
   *out = c;
   return FE_OK;
@@ -390,6 +391,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->d_cellG32); cudaFree(c->d_ptG32); cudaFree(c->d_ptC32); cudaFree(c->d_detJ);
   cudaFree(c->d_cellGff); cudaFree(c->d_ptGff); cudaFree(c->d_ptCff);
   cudaFree(c->d_status); cudaFree(c->d_stage);
+  cudaFree(c->d_tcimg[0]); cudaFree(c->d_tcimg[1]);
   if (c->copy_in) cudaStreamDestroy(c->copy_in);
   if (c->copy_out) cudaStreamDestroy(c->copy_out);
   for (cudaEvent_t ev : {c->ev_start, c->ev_in[0], c->ev_in[1], c->ev_comp[0], c->ev_comp[1], c->ev_out[0], c->ev_out[1]})
@@ -463,7 +465,9 @@ extern "C" fe_status fe_set_potential(fe_ctx* c, const double* Vq) {
 
 extern "C" fe_status fe_set_mode(fe_ctx* c, fe_mode m) {
   if (!c) return FE_EINVAL;
-  if (m != FE_FP64 && m != FE_FP32 && m != FE_TF32 && m != FE_BF16 && m != FE_TF32X3 && m != FE_DF64) return FE_EINVAL;
+  if (m != FE_FP64 && m != FE_FP32 && m != FE_TF32 && m != FE_BF16 && m != FE_TF32X3 && m != FE_DF64 &&
+      m != FE_BF16S)
+    return FE_EINVAL;
   c->mode = m;
   return FE_OK;
 }
@@ -488,8 +492,11 @@ extern "C" fe_status fe_set_tile(fe_ctx* c, fe_mode mode, int vectors_per_cta, i
     c->vb32 = vectors_per_cta;
     c->nty32 = lines;
     c->fp32_variant = variant;
+  } else if (mode == FE_TF32 || mode == FE_BF16) {
+    if (variant > 1) return FE_EINVAL;   // tensor-core tiles are fixed: only the kernel is chosen
+    c->tc_variant = variant;
   } else {
-    return FE_EUNSUPPORTED;  // tensor-core modes have a fixed 16-vector tile
+    return FE_EUNSUPPORTED;
   }
   return FE_OK;
 }

@@ -20,8 +20,9 @@ LIB_PATH = os.path.join(_HERE, "libfe.so")
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOTCONV, FE_EBREAKDOWN, FE_ENONFINITE, FE_ETIMEOUT, FE_EUNSUPPORTED = range(9)
 FE_BC_DIRICHLET0, FE_BC_PERIODIC = 0, 1
 FE_QUAD_GAUSS, FE_QUAD_GLL = 0, 1
-FE_FP64, FE_FP32, FE_TF32, FE_BF16, FE_TF32X3, FE_DF64 = 0, 1, 2, 3, 4, 5
-MODES = {"fp64": FE_FP64, "fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16, "tf32x3": FE_TF32X3, "df64": FE_DF64}
+FE_FP64, FE_FP32, FE_TF32, FE_BF16, FE_TF32X3, FE_DF64, FE_BF16S = 0, 1, 2, 3, 4, 5, 6
+MODES = {"fp64": FE_FP64, "fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16, "tf32x3": FE_TF32X3, "df64": FE_DF64,
+         "bf16s": FE_BF16S}
 
 
 class FeError(RuntimeError):
@@ -277,10 +278,15 @@ def fe_get_mode(ctx: int) -> int:
     return int(lib().fe_get_mode(ctx))
 
 
-def _check_block(ctx: int, t, what: str):
+def block_dtype(ctx: int):
+    """torch dtype of the blocks of the context's current mode."""
     import torch
     mode = fe_get_mode(ctx)
-    want = torch.float64 if mode in (FE_FP64, FE_DF64) else torch.float32
+    return torch.float64 if mode in (FE_FP64, FE_DF64) else torch.bfloat16 if mode == FE_BF16S else torch.float32
+
+
+def _check_block(ctx: int, t, what: str):
+    want = block_dtype(ctx)
     if not t.is_cuda or t.dtype != want or not t.is_contiguous() or t.dim() != 2 or t.shape[0] != fe_num_dofs(ctx):
         raise ValueError(f"{what}: need a contiguous CUDA {want} tensor of shape (num_dofs, n_vec)")
 
@@ -302,21 +308,19 @@ def _host_blocks(ctx: int, X, Y) -> int:
     writes exactly num_dofs * n_vec elements through the raw pointers, so a
     mismatch here would be an out-of-bounds host access there."""
     import torch
-    mode = fe_get_mode(ctx)
-    want = np.float64 if mode in (FE_FP64, FE_DF64) else np.float32
+    tdt = block_dtype(ctx)
+    want = {torch.float64: np.float64, torch.float32: np.float32}.get(tdt)   # numpy has no bfloat16
     n = fe_num_dofs(ctx)
     shapes = []
     for a, nm in ((X, "X"), (Y, "Y")):
         if isinstance(a, torch.Tensor):
-            ok = (not a.is_cuda and a.dtype == (torch.float64 if want is np.float64 else torch.float32)
-                  and a.is_contiguous())
+            ok = not a.is_cuda and a.dtype == tdt and a.is_contiguous()
         elif isinstance(a, np.ndarray):
-            ok = a.dtype == want and a.flags["C_CONTIGUOUS"]
+            ok = want is not None and a.dtype == want and a.flags["C_CONTIGUOUS"]
         else:
             ok = False
         if not ok or a.ndim != 2 or a.shape[0] != n:
-            raise ValueError(f"{nm}: need a C-contiguous host {np.dtype(want).name} block of shape "
-                             f"(num_dofs={n}, n_vec)")
+            raise ValueError(f"{nm}: need a C-contiguous host block of {tdt} of shape (num_dofs={n}, n_vec)")
         shapes.append(tuple(a.shape))
     if shapes[0] != shapes[1]:
         raise ValueError(f"X and Y must have the same shape, got {shapes[0]} and {shapes[1]}")

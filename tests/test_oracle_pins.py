@@ -377,3 +377,21 @@ def test_apply_rows_matches_csr():
         rows = np.arange(0, X.shape[0], 7)
         Yr = orc.apply_rows(mesh, p, nq, X, rows, Vq=V)
         np.testing.assert_allclose(Yr, Y[rows], atol=1e-13 * np.abs(Y).max())
+
+
+@pytest.mark.parametrize("periodic,distorted", [(False, False), (True, False), (False, True)])
+def test_row_block_assembly_equals_full_assembly(periodic, distorted):
+    """Rows assembled on their own are the rows of the full CSR matrix (same
+    sums, same merge), and their CSR x block product equals the oracle's
+    row-by-row product."""
+    from paper_2208_07129_gb300 import inputs
+    verts = inputs.perturbed_vertices(3, 2, 2, seed=5) if distorted else None
+    mesh = orc.Mesh(3, 2, 2, periodic=periodic, vertices=verts)
+    p, nq = 3, 5
+    V = np.random.default_rng(1).uniform(-1, 1, mesh.num_cells * nq ** 3)
+    A = orc.assemble(mesh, p, nq, Vq=V)
+    rows = np.array([0, 5, 17, 40, 41, 42, orc.num_dofs(mesh, p) - 1])
+    B = orc.assemble_rows(mesh, p, nq, rows, Vq=V)
+    np.testing.assert_array_equal(B.toarray(), A[rows].toarray())
+    X = np.random.default_rng(2).normal(size=(orc.num_dofs(mesh, p), 5))
+    np.testing.assert_allclose(orc.spmm(B, X), orc.apply_rows(mesh, p, nq, X, rows, Vq=V), rtol=1e-13, atol=1e-13)
