@@ -63,7 +63,173 @@ __global__ void col_sum_partials(const double* __restrict__ partial, int nblocks
 }
 
 template <typename T>
+cudaError_t col_dot(const T* a, const T* b, size_t n, int nv, double* partial, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// wide variants: 16-byte accesses (4 floats or 2 doubles of consecutive
+// columns per thread) and enough CTAs to fill every SM, for blocks whose
+// column count is a multiple of the vector width.  Same deterministic
+// per-CTA partials, summed in a fixed order.
+// ---------------------------------------------------------------------------
+
+constexpr int kWideBlocks = 152 * 8;
+
+template <typename T>
+struct Wide;
+template <>
+struct Wide<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static float get(const V& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+  __device__ static void set(V& v, int k, float x) {
+    if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
+  }
+};
+template <>
+struct Wide<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static double get(const V& v, int k) { return k == 0 ? v.x : v.y; }
+  __device__ static void set(V& v, int k, double x) {
+    if (k == 0) v.x = x; else v.y = x;
+  }
+};
+
+template <typename T>
+inline bool wide_ok(int nv, const void* const* ptrs, int n_ptrs) {
+  if (nv % Wide<T>::N != 0) return false;
+  for (int k = 0; k < n_ptrs; ++k)
+    if (ptrs[k] && (reinterpret_cast<uintptr_t>(ptrs[k]) & 15) != 0) return false;
+  return true;
+}
+
+// Rows of CTA b: [b * rows_per, ...); thread (x, y): column group x of the
+// CTA's column tile (32 groups of Wide<T>::N columns), rows y, y + 8, ...
+#define FE_WIDE_PROLOGUE(T)                                                            \
+  using W = Wide<T>;                                                                   \
+  using V = typename W::V;                                                             \
+  const int ncg = nv / W::N;                                                           \
+  const int cg = blockIdx.y * 32 + threadIdx.x;                                        \
+  const bool col_ok = cg < ncg;                                                        \
+  const size_t rows_per = (n + gridDim.x - 1) / gridDim.x;                             \
+  const size_t r0 = (size_t)blockIdx.x * rows_per;                                     \
+  const size_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
+
+// partial[b][c] over columns c of the thread's group
+template <typename T>
+__device__ __forceinline__ void wide_store_partials(double (&s)[Wide<T>::N], bool col_ok, int cg, int nv,
+                                                    double* __restrict__ partial) {
+  __shared__ double red[8][32][Wide<T>::N];
+#pragma unroll
+  for (int k = 0; k < Wide<T>::N; ++k) red[threadIdx.y][threadIdx.x][k] = s[k];
+  __syncthreads();
+  if (threadIdx.y == 0 && col_ok) {
+#pragma unroll
+    for (int k = 0; k < Wide<T>::N; ++k) {
+      double t = s[k];
+      for (int y = 1; y < 8; ++y) t += red[y][threadIdx.x][k];
+      partial[(size_t)blockIdx.x * nv + cg * Wide<T>::N + k] = t;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) col_dot_partial_wide(const T* __restrict__ a, const T* __restrict__ b,
+                                                            size_t n, int nv, double* __restrict__ partial) {
+  FE_WIDE_PROLOGUE(T)
+  double s[W::N] = {};
+  if (col_ok) {
+    for (size_t r = r0 + threadIdx.y; r < r1; r += 8) {
+      const V va = reinterpret_cast<const V*>(a + r * nv)[cg];
+      const V vb = reinterpret_cast<const V*>(b + r * nv)[cg];
+#pragma unroll
+      for (int k = 0; k < W::N; ++k) s[k] += (double)W::get(va, k) * (double)W::get(vb, k);
+    }
+  }
+  wide_store_partials<T>(s, col_ok, cg, nv, partial);
+}
+
+// x += alpha_c p, r -= alpha_c q, z = dinv .* r, partial r.z (one pass)
+template <typename T>
+__global__ void __launch_bounds__(256) cg_step_kernel_wide(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+                                                           const T* __restrict__ p, const T* __restrict__ q,
+                                                           const T* __restrict__ dinv,
+                                                           const double* __restrict__ alpha, size_t n, int nv,
+                                                           double* __restrict__ partial) {
+  FE_WIDE_PROLOGUE(T)
+  double s[W::N] = {};
+  if (col_ok) {
+    T a[W::N];
+#pragma unroll
+    for (int k = 0; k < W::N; ++k) a[k] = (T)alpha[cg * W::N + k];
+    for (size_t row = r0 + threadIdx.y; row < r1; row += 8) {
+      const size_t o = row * nv;
+      V vx = reinterpret_cast<const V*>(x + o)[cg];
+      V vr = reinterpret_cast<const V*>(r + o)[cg];
+      const V vp = reinterpret_cast<const V*>(p + o)[cg];
+      const V vq = reinterpret_cast<const V*>(q + o)[cg];
+      const T d = dinv ? dinv[row] : T(1);
+      V vz;
+#pragma unroll
+      for (int k = 0; k < W::N; ++k) {
+        W::set(vx, k, W::get(vx, k) + a[k] * W::get(vp, k));
+        const T rn = W::get(vr, k) - a[k] * W::get(vq, k);
+        W::set(vr, k, rn);
+        const T zn = rn * d;
+        W::set(vz, k, zn);
+        s[k] += (double)rn * (double)zn;
+      }
+      reinterpret_cast<V*>(x + o)[cg] = vx;
+      reinterpret_cast<V*>(r + o)[cg] = vr;
+      reinterpret_cast<V*>(z + o)[cg] = vz;
+    }
+  }
+  wide_store_partials<T>(s, col_ok, cg, nv, partial);
+}
+
+// p = z + beta_c p
+template <typename T>
+__global__ void __launch_bounds__(256) cg_direction_kernel_wide(T* __restrict__ p, const T* __restrict__ z,
+                                                                const double* __restrict__ beta, size_t n, int nv) {
+  FE_WIDE_PROLOGUE(T)
+  if (!col_ok) return;
+  T bc[W::N];
+#pragma unroll
+  for (int k = 0; k < W::N; ++k) bc[k] = (T)beta[cg * W::N + k];
+  for (size_t row = r0 + threadIdx.y; row < r1; row += 8) {
+    const size_t o = row * nv;
+    V vp = reinterpret_cast<const V*>(p + o)[cg];
+    const V vz = reinterpret_cast<const V*>(z + o)[cg];
+#pragma unroll
+    for (int k = 0; k < W::N; ++k) W::set(vp, k, W::get(vz, k) + bc[k] * W::get(vp, k));
+    reinterpret_cast<V*>(p + o)[cg] = vp;
+  }
+}
+#undef FE_WIDE_PROLOGUE
+
+// out[c] = sum_b partial[b * nv + c]: one warp per column, lane l adds the
+// partials l, l + 32, ... in order, then a fixed butterfly (deterministic).
+__global__ void col_sum_partials_warp(const double* __restrict__ partial, int nblocks, int nv,
+                                      double* __restrict__ out) {
+  const int c = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (c >= nv) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)b * nv + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = s;
+}
+
+inline dim3 wide_grid(int nv, int vec) { return dim3(kWideBlocks, (unsigned)((nv / vec + 31) / 32)); }
+
+template <typename T>
 cudaError_t col_dot(const T* a, const T* b, size_t n, int nv, double* partial, double* out, cudaStream_t s) {
+  const void* ptrs[2] = {a, b};
+  if (wide_ok<T>(nv, ptrs, 2)) {
+    col_dot_partial_wide<T><<<wide_grid(nv, Wide<T>::N), dim3(32, 8), 0, s>>>(a, b, n, nv, partial);
+    col_sum_partials_warp<<<(nv + 7) / 8, 256, 0, s>>>(partial, kWideBlocks, nv, out);
+    return cudaGetLastError();
+  }
   dim3 grid(kRedBlocks, (nv + kColTile - 1) / kColTile);
   col_dot_partial<T><<<grid, dim3(kColTile, 8), 0, s>>>(a, b, n, nv, partial);
   col_sum_partials<<<(nv + 127) / 128, 128, 0, s>>>(partial, kRedBlocks, nv, out);
@@ -238,7 +404,7 @@ cudaError_t solver_workspace(fe_ctx* c, int nv) {
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = grow(&w.v64[k], &w.cap64[k], tot);
   for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = grow(&w.v32[k], &w.cap32[k], tot);
   if (e == cudaSuccess) e = grow(&w.colbuf, &w.cap_col, (size_t)nv * 12);
-  if (e == cudaSuccess) e = grow(&w.partial, &w.cap_partial, (size_t)kRedBlocks * nv);
+  if (e == cudaSuccess) e = grow(&w.partial, &w.cap_partial, (size_t)kWideBlocks * nv);
   if (e == cudaSuccess) e = grow(&w.active, &w.cap_active, (size_t)nv);
   if (e == cudaSuccess && !w.dinv64) {
     e = cudaMalloc(&w.dinv64, n * sizeof(double));
@@ -293,6 +459,8 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
   const T* dinv_all = (const T*)(sizeof(T) == 8 ? (const void*)w.dinv64 : (const void*)w.dinv32);
   if (precond == FE_PRECOND_JACOBI) dinv = dinv_all;
   const bool learned = precond == FE_PRECOND_LEARNED;
+  const void* vecs[6] = {x, r, z, p, q, b};
+  const bool wide = wide_ok<T>(nv, vecs, 6);
   cudaError_t e;
   std::vector<double> rr_h(nv);
   std::vector<int> act_h(nv, 1);
@@ -330,9 +498,15 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
       if (st != FE_OK) return st;
       if ((e = col_dot<T>(r, z, n, nv, w.partial, rznew, s)) != cudaSuccess) return from_cuda(e);
     } else {
-      const dim3 grid(kRedBlocks, (nv + kColTile - 1) / kColTile);
-      cg_step_kernel<T><<<grid, dim3(kColTile, 8), 0, s>>>(x, r, z, p, q, dinv, alpha, n, nv, w.partial);
-      col_sum_partials<<<(nv + 127) / 128, 128, 0, s>>>(w.partial, kRedBlocks, nv, rznew);
+      if (wide) {
+        cg_step_kernel_wide<T><<<wide_grid(nv, Wide<T>::N), dim3(32, 8), 0, s>>>(x, r, z, p, q, dinv, alpha, n, nv,
+                                                                                 w.partial);
+        col_sum_partials_warp<<<(nv + 7) / 8, 256, 0, s>>>(w.partial, kWideBlocks, nv, rznew);
+      } else {
+        const dim3 grid(kRedBlocks, (nv + kColTile - 1) / kColTile);
+        cg_step_kernel<T><<<grid, dim3(kColTile, 8), 0, s>>>(x, r, z, p, q, dinv, alpha, n, nv, w.partial);
+        col_sum_partials<<<(nv + 127) / 128, 128, 0, s>>>(w.partial, kRedBlocks, nv, rznew);
+      }
     }
     if (learned) {
       fcg_safeguard_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv_all, z, rznew, tot, nv);
@@ -341,8 +515,11 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
       if ((e = col_dot<T>(z, q, n, nv, w.partial, rzmid, s)) != cudaSuccess) return from_cuda(e);
     }
     cg_beta_kernel<<<(nv + 127) / 128, 128, 0, s>>>(rznew, rzmid, pq, rz, w.active, beta, nv, learned ? 1 : 0);
-    cg_direction_kernel<T><<<dim3(kRedBlocks, (nv + kColTile - 1) / kColTile), dim3(kColTile, 8), 0, s>>>(
-        p, z, beta, n, nv);
+    if (wide)
+      cg_direction_kernel_wide<T><<<wide_grid(nv, Wide<T>::N), dim3(32, 8), 0, s>>>(p, z, beta, n, nv);
+    else
+      cg_direction_kernel<T><<<dim3(kRedBlocks, (nv + kColTile - 1) / kColTile), dim3(kColTile, 8), 0, s>>>(
+          p, z, beta, n, nv);
     ++it;
     if (hook) hook(hook_user, it, x, r, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return from_cuda(e);

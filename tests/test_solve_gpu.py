@@ -41,8 +41,11 @@ def _problem(fe, nx=3, p=4, nq=6, n_vec=6, distorted=False, seed=0):
 @pytest.mark.parametrize("precond,inner", [("jacobi", "fp64"), ("none", "fp64"), ("jacobi", "fp32"),
                                            ("jacobi", "tf32"), ("jacobi", "bf16"), ("jacobi", "tf32x3"),
                                            ("jacobi", "df64")])
-def test_pcg_solution(fe, precond, inner):
-    ctx, B, Xref = _problem(fe, distorted=(inner != "fp64"))
+@pytest.mark.parametrize("n_vec", [6, 8], ids=["nv6", "nv8"])
+def test_pcg_solution(fe, precond, inner, n_vec):
+    """n_vec = 8 runs the 16-byte vector kernels in FP64 and FP32; n_vec = 6
+    runs them in FP64 only (FP32 needs a multiple of 4 columns)."""
+    ctx, B, Xref = _problem(fe, n_vec=n_vec, distorted=(inner != "fp64"))
     try:
         Bd = torch.from_numpy(B).cuda()
         Xd = torch.zeros_like(Bd)
