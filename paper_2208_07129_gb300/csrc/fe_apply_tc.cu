@@ -92,20 +92,16 @@ template <int E, int G, int KIND, typename TIO, bool GEN>
 cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, TIO* Y, int n_vec, cudaStream_t s) {
   using SH = TcShape<E, G, KIND>;
   auto kern = tc_apply_kernel<E, G, KIND, TIO, GEN>;
-  // Request enough shared memory that the CTAs one SM can hold never need
-  // more tensor-memory columns than the SM has (512): a CTA whose alloc
-  // could not be served would wait for a column release.
-  size_t smem = SH::SMEM_BYTES;
-  const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
-  const int tmem_ctas = 512 / SH::TMEM_COLS;
-  if (per_sm / (smem + per_cta_reserved) > (size_t)tmem_ctas) smem = per_sm / tmem_ctas - per_cta_reserved + 16;
+  // One CTA per SM: its shared-memory request (more than half of an SM's)
+  // keeps a second CTA, which would need tensor-memory columns the first
+  // holds, off the SM.
+  constexpr size_t smem = SH::SMEM_BYTES;
+  static_assert(2 * (SH::SMEM_BYTES + 1024) > 228 * 1024, "two CTAs must not fit on one SM");
   cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, occ = 0;
+  int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem)) != cudaSuccess) return e;
-  if (occ < 1) return cudaErrorInvalidConfiguration;
   const Geom<float> geo = make_geom<float>(c);
   const TcArgs a{img, c->np, c->nq, c->d_status};
   const int n_vb = (n_vec + kTcVectors - 1) / kTcVectors;
@@ -114,8 +110,9 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
     if (n == 0) continue;
     const long long tasks = (long long)n * n_vb;
     if (tasks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const int grid = (int)std::min<long long>(tasks, (long long)occ * sms);
-    kern<<<grid, 128, smem, s>>>(a, c->mdev, geo, c->d_cells + c->colors.offset[k], (int)tasks, n_vec, n_vb, X, Y);
+    const int grid = (int)std::min<long long>((tasks + SH::SLOTS - 1) / SH::SLOTS, (long long)sms);
+    kern<<<grid, 128 * SH::SLOTS, smem, s>>>(a, c->mdev, geo, c->d_cells + c->colors.offset[k], (int)tasks, n_vec,
+                                              n_vb, X, Y);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -63,6 +63,7 @@ struct TcShape {
   static constexpr int ROWS = LINES * kTcVectors;
   static constexpr int T = (ROWS + 127) / 128;                // M = 128 tiles per pass
   static_assert(E % G == 0 && G * ES == 4, "a packed store holds G operands in 4 bytes");
+  static_assert(16 % H == 0, "a thread's line-group index b is the same in every tile");
   __host__ __device__ static constexpr int Kr(int s) { return tc_round_up(G * tc_kline(s) * E, KI); }
   __host__ __device__ static constexpr int Nr(int s) { return tc_round_up(G * tc_nline(s) * E, 16); }
   __host__ __device__ static constexpr int b_off(int s) {
@@ -81,9 +82,18 @@ struct TcShape {
     for (int s = 0; s < 6; ++s) m = T * Nr(s) > m ? T * Nr(s) : m;
     return m;
   }
-  static constexpr int TMEM_COLS = d_cols_max() <= 32 ? 32 : d_cols_max() <= 64 ? 64 : d_cols_max() <= 128 ? 128
+  static constexpr int SLOT_COLS = d_cols_max() <= 32 ? 32 : d_cols_max() <= 64 ? 64 : d_cols_max() <= 128 ? 128
                                    : d_cols_max() <= 256 ? 256 : 512;
-  static constexpr int SMEM_BYTES = B_BYTES + S_BYTES + M_BYTES + 64;
+  // Task slots per CTA (one warpgroup each, own tensor-memory columns and A
+  // buffers, one shared copy of the B operands): as many as 227 KB of shared
+  // memory and the 512 tensor-memory columns allow, at most 4.
+  static constexpr int SLOT_BYTES = S_BYTES + M_BYTES;
+  static constexpr int SLOTS_SMEM = (227 * 1024 - B_BYTES - 256) / SLOT_BYTES;
+  static constexpr int SLOTS = SLOTS_SMEM < 512 / SLOT_COLS ? (SLOTS_SMEM < 4 ? SLOTS_SMEM : 4)
+                                                            : (512 / SLOT_COLS < 4 ? 512 / SLOT_COLS : 4);
+  static constexpr int TMEM_COLS = SLOTS * SLOT_COLS <= 128 ? 128 : SLOTS * SLOT_COLS <= 256 ? 256 : 512;
+  static constexpr int SMEM_BYTES = B_BYTES + SLOTS * SLOT_BYTES + 128;
+  static_assert(SLOTS >= 1, "one task slot must fit");
 };
 
 // Byte offset of element (row, k) of a K-major operand whose rows hold kr values.
@@ -101,18 +111,13 @@ __device__ __forceinline__ uint32_t tc_pack2(float x0, float x1) { return pack_b
 
 template <typename TIO>
 __device__ __forceinline__ float tc_load(const TIO* p) {
-  if constexpr (sizeof(TIO) == 4) return __ldg(reinterpret_cast<const float*>(p));
+  if constexpr (sizeof(TIO) == 4) return *reinterpret_cast<const float*>(p);
   else return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
 }
 template <typename TIO>
-__device__ __forceinline__ void tc_store(TIO* p, float v, bool add) {
-  if constexpr (sizeof(TIO) == 4) {
-    float* q = reinterpret_cast<float*>(p);
-    *q = add ? *q + v : v;
-  } else {
-    __nv_bfloat16* q = reinterpret_cast<__nv_bfloat16*>(p);
-    *q = __float2bfloat16_rn(add ? __bfloat162float(*q) + v : v);
-  }
+__device__ __forceinline__ void tc_store(TIO* p, float v) {
+  if constexpr (sizeof(TIO) == 4) *reinterpret_cast<float*>(p) = v;
+  else *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
 }
 
 struct TcArgs {
@@ -125,22 +130,30 @@ struct TcArgs {
 // The row's line group has slow coordinate `a` and lines f = G b + g; D
 // column (g, qty, n) is quantity qty at output index n of line g.  SLOWN:
 // the next pass's slow coordinate is n (F-x, B-z), else it stays a (F-y, B-y).
+// Every quantity block starts on a core-matrix boundary (E a multiple of
+// KC), so the address of word (n, qty) is a per-thread base plus a
+// compile-time offset: one packed store per word.
 template <class SH, int NQT, bool SLOWN, int KRN>
 __device__ __forceinline__ void tc_write_transposed(const float* d, int a, int b, int v, unsigned char* Mb) {
-  constexpr int E = SH::E, G = SH::G, H = SH::H;
-  constexpr int NL = NQT * E;   // D columns per line = K per line of the next pass
+  constexpr int E = SH::E, G = SH::G, H = SH::H, KC = SH::KC, ES = SH::ES;
+  constexpr int NL = NQT * E;              // D columns per line = K per line of the next pass
+  constexpr int RB = (KRN / KC) * 128;     // bytes per group of 8 rows of the next pass's A
+  static_assert(E % KC == 0 && NL % KC == 0, "quantity blocks must start on core-matrix boundaries");
+  const int kb = G * b;                    // k of the first line of the group inside its quantity block
+  int base = (kb / KC) * 128 + v * 16 + (kb % KC) * ES;
+  if (SLOWN) base += (a / G) * RB + ((a % G) * NL / KC) * 128;
+  else base += a * H * RB;
+  unsigned char* p = Mb + base;
 #pragma unroll
   for (int n = 0; n < E; ++n) {
-    const int ap = SLOWN ? n : a, fp = SLOWN ? a : n;
-    const int rowp = (ap * H + fp / G) * kTcVectors + v;
-    const int gp = fp % G;
 #pragma unroll
     for (int q = 0; q < NQT; ++q) {
-      const int k = gp * NL + q * E + G * b;
+      const int off = SLOWN ? n * H * RB + q * (E / KC) * 128
+                            : (n / G) * RB + ((n % G) * NL / KC) * 128 + q * (E / KC) * 128;
       uint32_t w;
       if constexpr (G == 1) w = tc_pack1<SH::KIND>(d[q * E + n]);
       else w = tc_pack2<SH::KIND>(d[q * E + n], d[NL + q * E + n]);
-      *reinterpret_cast<uint32_t*>(Mb + tc_off<SH::ES>(rowp, k, KRN)) = w;
+      *reinterpret_cast<uint32_t*>(p + off) = w;
     }
   }
 }
@@ -182,22 +195,40 @@ __device__ __forceinline__ void tc_issue(uint32_t tmem, const unsigned char* A, 
   umma_commit(mbar);
 }
 
-// One persistent CTA per slot: loops over the (cell, 8-vector block) tasks of
-// one colour.  128 threads: thread t owns TMEM lane t, i.e. row t of every
-// 128-row tile of a pass.
+// Named barrier of the 128 threads of one task slot (ids 1..4; 0 is the CTA
+// barrier), plain and with an OR reduction of a predicate.
+__device__ __forceinline__ void slot_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ bool slot_sync_or(int id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %2, 0;\nbar.red.or.pred p, %1, 128, q;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"(id), "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+// One persistent CTA per SM with SH::SLOTS task slots.  Slot s is warpgroup s
+// (threads 128 s ... 128 s + 127): it loops over the (cell, 8-vector block)
+// tasks s, s + SLOTS, ... of this CTA's share of one colour, with its own
+// tensor-memory columns, A buffers and mbarrier, so the slots' passes overlap
+// one another's latencies.  Thread lt of a slot owns TMEM lane lt, i.e. row
+// lt of every 128-row tile of a pass.
 template <int E, int G, int KIND, typename TIO, bool GEN>
-__global__ void __launch_bounds__(128) tc_apply_kernel(const TcArgs args, const MeshDev m, const Geom<float> geo,
-                                                       const int* __restrict__ cells, int n_tasks, int n_vec,
-                                                       int n_vb, const TIO* __restrict__ X, TIO* __restrict__ Y) {
+__global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
+    tc_apply_kernel(const TcArgs args, const MeshDev m, const Geom<float> geo, const int* __restrict__ cells,
+                    int n_tasks, int n_vec, int n_vb, const TIO* __restrict__ X, TIO* __restrict__ Y) {
   using SH = TcShape<E, G, KIND>;
-  constexpr int H = SH::H, T = SH::T;
+  constexpr int H = SH::H, T = SH::T, SLOTS = SH::SLOTS;
   extern __shared__ __align__(128) unsigned char smem[];
+  const int t = threadIdx.x, warp = t >> 5, slot = t >> 7, lt = t & 127;
   unsigned char* Bs = smem;
-  unsigned char* Sb = smem + SH::B_BYTES;
+  unsigned char* Sb = smem + SH::B_BYTES + slot * SH::SLOT_BYTES;
   unsigned char* Mb = Sb + SH::S_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Mb + SH::M_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  const int t = threadIdx.x, warp = t >> 5;
+  uint64_t* mbars = reinterpret_cast<uint64_t*>(smem + SH::B_BYTES + SLOTS * SH::SLOT_BYTES);
+  uint64_t* mbar = mbars + slot;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbars + SLOTS);
+  const int bar = 1 + slot;
   const int np = args.np, nq = args.nq, P = np - 1;
   const int nq3 = nq * nq * nq;
 
@@ -206,94 +237,115 @@ __global__ void __launch_bounds__(128) tc_apply_kernel(const TcArgs args, const 
                  "r"(SH::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (t == 0) mbar_init(mbar, 1);
-  {  // B operands -> shared; the A buffers start at zero (padding stays finite)
+  if (lt == 0) mbar_init(mbar, 1);
+  {  // B operands -> shared (once per CTA); the A buffers start at zero
     const uint4* src = reinterpret_cast<const uint4*>(args.bimg);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
-    for (int k = t; k < SH::B_BYTES / 16; k += 128) dst[k] = __ldg(src + k);
-    uint4* z = reinterpret_cast<uint4*>(Sb);
-    for (int k = t; k < (SH::S_BYTES + SH::M_BYTES) / 16; k += 128) z[k] = make_uint4(0, 0, 0, 0);
+    for (int k = t; k < SH::B_BYTES / 16; k += blockDim.x) dst[k] = __ldg(src + k);
+    uint4* z = reinterpret_cast<uint4*>(smem + SH::B_BYTES);
+    for (int k = t; k < SLOTS * SH::SLOT_BYTES / 16; k += blockDim.x) z[k] = make_uint4(0, 0, 0, 0);
   }
   fence_async_smem();
   asm volatile("fence.mbarrier_init.release.cluster;");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tmem = *tslot + (uint32_t)(slot * SH::SLOT_COLS);
+  const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   bool fail = false;
 
-  for (int task = blockIdx.x; task < n_tasks && !fail; task += gridDim.x) {
+  for (int task = blockIdx.x * SLOTS + slot; task < n_tasks && !fail; task += gridDim.x * SLOTS) {
     const int e = cells[task / n_vb];
     const int v0 = (task % n_vb) * kTcVectors;
     const int cx = e % m.nx, cy = (e / m.nx) % m.ny, cz = e / (m.nx * m.ny);
+    // This thread's rows: tile j, line group L = 16 j + lt / 8 = (slow, b)
+    // with b = (lt / 8) % H fixed and slow = (16 j + lt / 8) / H; vector v.
+    const int v = lt & 7, bq = (lt >> 3) % H;
+    const bool vok = v0 + v < n_vec;
+    // Per-task node tables along x (all E entries) and along the thread's
+    // G lines in y: offsets in elements, and bit masks of the nodes that
+    // exist and are free (valid) and of those this cell writes first.
+    int xo[E];
+    unsigned xv = 0, xf = 0;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int gx = node_coord(cx, i, P, m.Nx, m.periodic);
+      xo[i] = gx * n_vec;
+      if (i < np && !on_boundary(gx, m.Nx, m.periodic)) xv |= 1u << i;
+      if (i < np && first_along(cx, m.nx, i, P, m.periodic, m.last_odd_x)) xf |= 1u << i;
+    }
+    int yo[G];
+    unsigned yv = 0, yf = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int i2 = G * bq + g;
+      const int gy = node_coord(cy, i2, P, m.Ny, m.periodic);
+      yo[g] = gy * m.Nx * n_vec;
+      if (i2 < np && !on_boundary(gy, m.Ny, m.periodic)) yv |= 1u << g;
+      if (i2 < np && first_along(cy, m.ny, i2, P, m.periodic, m.last_odd_y)) yf |= 1u << g;
+    }
+    const size_t plane = (size_t)m.Nx * m.Ny * n_vec;
 
-    // ---- gather: row (i3, b) x v, lines i2 = G b + g, K = [g][i1] ----
+    // ---- gather: row (i3, b) x v, lines i2 = G b + g, K = [g][i1]; every
+    // load of the thread is issued before the first use ----
 #pragma unroll
     for (int j = 0; j < T; ++j) {
-      const int r = j * 128 + t, L = r >> 3, v = r & 7;
+      const int r = j * 128 + lt, L = r >> 3;
       if (L >= SH::LINES) continue;
-      const int i3 = L / H, b = L % H;
-      const bool vok = v0 + v < n_vec;
+      const int i3 = L / H;
+      const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
+      const bool zok = vok && i3 < np && !on_boundary(gz, m.Nz, m.periodic);
+      const TIO* xz = X + (size_t)gz * plane + v0 + v;
       float vals[SH::Kr(0)];
 #pragma unroll
-      for (int k = 0; k < SH::Kr(0); ++k) vals[k] = 0.f;
-      const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
-      const bool con_z = i3 >= np || on_boundary(gz, m.Nz, m.periodic);
-#pragma unroll
       for (int g = 0; g < G; ++g) {
-        const int i2 = G * b + g;
-        const int gy = node_coord(cy, i2, P, m.Ny, m.periodic);
-        if (!vok || con_z || i2 >= np || on_boundary(gy, m.Ny, m.periodic)) continue;
-        const size_t rowoff = (size_t)(gy + (size_t)m.Ny * gz) * m.Nx;
+        const bool ok = zok && ((yv >> g) & 1u);
 #pragma unroll
-        for (int i1 = 0; i1 < E; ++i1) {
-          if (i1 >= np) continue;
-          const int gx = node_coord(cx, i1, P, m.Nx, m.periodic);
-          if (on_boundary(gx, m.Nx, m.periodic)) continue;
-          vals[g * E + i1] = tc_load(X + (rowoff + gx) * n_vec + v0 + v);
-        }
+        for (int i1 = 0; i1 < E; ++i1)
+          vals[g * E + i1] = (ok && ((xv >> i1) & 1u)) ? tc_load(xz + yo[g] + xo[i1]) : 0.f;
       }
+#pragma unroll
+      for (int k = G * E; k < SH::Kr(0); ++k) vals[k] = 0.f;
       tc_write_row<SH, SH::Kr(0)>(vals, r, Sb);
     }
 
     // ---- the six passes ----
-    // pass index s = 0..5, mbarrier phase = s & 1 (six completions per task)
+    // pass index s = 0..5, mbarrier phase = s & 1 (six completions per task).
     // Every thread's writes of the A operand become visible to the tensor
-    // cores, thread 0 issues the pass, everyone waits for its completion
-    // (bounded; a timeout anywhere ends the loop for the whole CTA).  The
-    // pass reads A from shared memory and writes D to tensor memory only, so
-    // the next A may overwrite this one as soon as the pass is complete.
+    // cores, the slot's thread 0 issues the pass, the slot waits for its
+    // completion (bounded; a timeout anywhere ends the slot's loop).  The pass
+    // reads A from shared memory and writes D to tensor memory only, so the
+    // next A may overwrite this one as soon as the pass is complete.
 #define FE_TC_ISSUE(S, ABUF)                                                   \
   fence_async_smem();                                                          \
   tc_fence_before();                                                           \
-  __syncthreads();                                                             \
-  if (t == 0) tc_issue<SH, S>(tmem, ABUF, Bs, mbar);                           \
-  if (__syncthreads_or(!mbar_wait(mbar, (S) & 1))) { fail = true; break; }      \
+  slot_sync(bar);                                                              \
+  if (lt == 0) tc_issue<SH, S>(tmem, ABUF, Bs, mbar);                          \
+  if (slot_sync_or(bar, !mbar_wait(mbar, (S) & 1))) { fail = true; break; }    \
   tc_fence_after();
 
     FE_TC_ISSUE(0, Sb)
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < T; ++j) {   // F-x: row (i3, b), lines i2 -> A of F-y: (q1, i3 / G)
       float d[SH::Nr(0)];
       tmem_load<SH::Nr(0)>(tlane + j * SH::Nr(0), d);
-      const int r = j * 128 + t, L = r >> 3;
+      const int r = j * 128 + lt, L = r >> 3;
       if (L < SH::LINES) tc_write_transposed<SH, 2, true, SH::Kr(1)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(1, Mb)
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < T; ++j) {   // F-y: row (q1, b), lines i3 -> A of F-z: (q1, q2 / G)
       float d[SH::Nr(1)];
       tmem_load<SH::Nr(1)>(tlane + j * SH::Nr(1), d);
-      const int r = j * 128 + t, L = r >> 3;
+      const int r = j * 128 + lt, L = r >> 3;
       if (L < SH::LINES) tc_write_transposed<SH, 3, false, SH::Kr(2)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(2, Mb)
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < T; ++j) {   // F-z and the quadrature-point operation: row (q1, b), lines q2 = G b + g
       float d[SH::Nr(2)];
       tmem_load<SH::Nr(2)>(tlane + j * SH::Nr(2), d);
-      const int r = j * 128 + t, L = r >> 3;
+      const int r = j * 128 + lt, L = r >> 3;
       if (L >= SH::LINES) continue;
       const int q1 = L / H, b = L % H;
       float g00 = 0.f, g01 = 0.f, g02 = 0.f, g11 = 0.f, g12 = 0.f, g22 = 0.f;
@@ -306,13 +358,18 @@ __global__ void __launch_bounds__(128) tc_apply_kernel(const TcArgs args, const 
       for (int g = 0; g < G; ++g) {
         const int q2 = G * b + g;
         float* dl = d + g * 4 * E;   // [val | dz | dy | dx] along q3, becomes [hv | hz | hy | hx]
+        float cv[E];
 #pragma unroll
         for (int q3 = 0; q3 < E; ++q3) {
-          float hv = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+          const bool ok = q1 < nq && q2 < nq && q3 < nq;
+          cv[q3] = ok ? __ldg(geo.ptC + (size_t)e * nq3 + q1 + nq * (q2 + nq * q3)) : 0.f;
+        }
+#pragma unroll
+        for (int q3 = 0; q3 < E; ++q3) {
+          float hx = 0.f, hy = 0.f, hz = 0.f;
           if (q1 < nq && q2 < nq && q3 < nq) {
-            const int Q = q1 + nq * (q2 + nq * q3);
             if (GEN) {
-              const float* pg = geo.ptG + (size_t)e * 6 * nq3 + Q;
+              const float* pg = geo.ptG + (size_t)e * 6 * nq3 + q1 + nq * (q2 + nq * q3);
               g00 = __ldg(pg); g01 = __ldg(pg + nq3); g02 = __ldg(pg + 2 * nq3);
               g11 = __ldg(pg + 3 * nq3); g12 = __ldg(pg + 4 * nq3); g22 = __ldg(pg + 5 * nq3);
             }
@@ -320,9 +377,8 @@ __global__ void __launch_bounds__(128) tc_apply_kernel(const TcArgs args, const 
             hx = g00 * dx + g01 * dy + g02 * dz;
             hy = g01 * dx + g11 * dy + g12 * dz;
             hz = g02 * dx + g12 * dy + g22 * dz;
-            hv = __ldg(geo.ptC + (size_t)e * nq3 + Q) * dl[q3];
           }
-          dl[q3] = hv;
+          dl[q3] = cv[q3] * dl[q3];
           dl[E + q3] = hz;
           dl[2 * E + q3] = hy;
           dl[3 * E + q3] = hx;
@@ -331,65 +387,71 @@ __global__ void __launch_bounds__(128) tc_apply_kernel(const TcArgs args, const 
       tc_write_row<SH, SH::Kr(3)>(d, r, Mb);
     }
     FE_TC_ISSUE(3, Mb)
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < T; ++j) {   // B-z: row (q1, b), lines q2 -> A of B-y: (i3, q1 / G)
       float d[SH::Nr(3)];
       tmem_load<SH::Nr(3)>(tlane + j * SH::Nr(3), d);
-      const int r = j * 128 + t, L = r >> 3;
+      const int r = j * 128 + lt, L = r >> 3;
       if (L < SH::LINES) tc_write_transposed<SH, 3, true, SH::Kr(4)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(4, Mb)
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < T; ++j) {   // B-y: row (i3, b), lines q1 -> A of B-x: (i3, i2 / G)
       float d[SH::Nr(4)];
       tmem_load<SH::Nr(4)>(tlane + j * SH::Nr(4), d);
-      const int r = j * 128 + t, L = r >> 3;
+      const int r = j * 128 + lt, L = r >> 3;
       if (L < SH::LINES) tc_write_transposed<SH, 2, false, SH::Kr(5)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(5, Mb)
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < T; ++j) {   // B-x and assembly: row (i3, b), lines i2 = G b + g, D = [g][i1]
       float d[SH::Nr(5)];
       tmem_load<SH::Nr(5)>(tlane + j * SH::Nr(5), d);
-      const int r = j * 128 + t, L = r >> 3, v = r & 7;
-      if (L >= SH::LINES || v0 + v >= n_vec) continue;
-      const int i3 = L / H, b = L % H;
+      const int r = j * 128 + lt, L = r >> 3;
+      if (L >= SH::LINES || !vok) continue;
+      const int i3 = L / H;
       if (i3 >= np) continue;
       const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
-      const bool con_z = on_boundary(gz, m.Nz, m.periodic);
-      const bool first_z = first_along(cz, m.nz, i3, P, m.periodic, m.last_odd_z);
+      const bool zcon = on_boundary(gz, m.Nz, m.periodic);
+      const bool zfirst = first_along(cz, m.nz, i3, P, m.periodic, m.last_odd_z);
+      TIO* yz = Y + (size_t)gz * plane + v0 + v;
+      // every read of Y (the partial sums of earlier colours) is issued
+      // before the first store, so the loads overlap
+      float old[G * E];
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        const int i2 = G * b + g;
-        if (i2 >= np) continue;
-        const int gy = node_coord(cy, i2, P, m.Ny, m.periodic);
-        const bool con_yz = con_z || on_boundary(gy, m.Ny, m.periodic);
-        const bool first_yz = first_z && first_along(cy, m.ny, i2, P, m.periodic, m.last_odd_y);
-        const size_t rowoff = (size_t)(gy + (size_t)m.Ny * gz) * m.Nx;
+        const unsigned rd = (zcon || !((yv >> g) & 1u)) ? 0u
+                            : xv & ~((zfirst && ((yf >> g) & 1u)) ? xf : 0u);
+#pragma unroll
+        for (int i1 = 0; i1 < E; ++i1) old[g * E + i1] = ((rd >> i1) & 1u) ? tc_load(yz + yo[g] + xo[i1]) : 0.f;
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        if (G * bq + g >= np) continue;
+        const bool ycon = zcon || !((yv >> g) & 1u);
+        const unsigned first = (zfirst && ((yf >> g) & 1u)) ? xf : 0u;
+        const unsigned valid = ycon ? 0u : xv;
 #pragma unroll
         for (int i1 = 0; i1 < E; ++i1) {
           if (i1 >= np) continue;
-          const int gx = node_coord(cx, i1, P, m.Nx, m.periodic);
-          const bool con = con_yz || on_boundary(gx, m.Nx, m.periodic);
-          const bool first = first_yz && first_along(cx, m.nx, i1, P, m.periodic, m.last_odd_x);
-          TIO* dst = Y + (rowoff + gx) * n_vec + v0 + v;
-          if (first) tc_store(dst, con ? 0.f : d[g * E + i1], false);
-          else if (!con) tc_store(dst, d[g * E + i1], true);
+          TIO* dst = yz + yo[g] + xo[i1];
+          if ((first >> i1) & 1u) tc_store(dst, ((valid >> i1) & 1u) ? d[g * E + i1] : 0.f);
+          else if ((valid >> i1) & 1u) tc_store(dst, old[g * E + i1] + d[g * E + i1]);
         }
       }
     }
 #undef FE_TC_ISSUE
   }
 
-  if (fail && t == 0) {
+  if (fail && lt == 0) {
     atomicMax(args.status, (int)FE_ETIMEOUT);
-    // let any MMA still in flight finish before the tensor memory is released
+    // let any MMA of this slot still in flight finish before the tensor memory is released
     mbar_wait(mbar, 0, 1 << 20);
     mbar_wait(mbar, 1, 1 << 20);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(SH::TMEM_COLS));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(SH::TMEM_COLS));
 }
 
 }  // namespace fe
