@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_precond_kernel(const MlpAr
   __syncthreads();
   // gather the patch of column `col` (row `row` of the tile), 8 nodes per 16-byte chunk
   float ss = 0.f;
-#pragma unroll 2
+#pragma unroll 4
   for (int kg = half; kg < a.K1 / 8; kg += 2) {
     float v[8];
 #pragma unroll
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_precond_kernel(const MlpAr
                 idesc, k > 0);
     umma_commit(mbar);
   }
-  bool ok = mbar_wait(mbar, 0);
+  bool ok = mbar_wait_timed(mbar, 0);
   asm volatile("tcgen05.fence::after_thread_sync;");
   // every thread must see GEMM1 complete before the patch tile is overwritten
   __syncthreads();
@@ -232,18 +232,27 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_precond_kernel(const MlpAr
     }
     umma_commit(mbar);
   }
-  if (ok) ok = mbar_wait(mbar, 1);
+  if (ok) ok = mbar_wait_timed(mbar, 1);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     for (int c0 = half * 32; c0 < a.K1; c0 += 64) {
       float d[32];
       tmem_ld32(lane_base + kHidden + c0, d);
       if (!active) continue;
+      // all 32 reads of z are issued before the first store (a store may
+      // alias a later read as far as the compiler knows), so they overlap
+      float zold[32];
 #pragma unroll
       for (int u = 0; u < 32; ++u) {
         const int i = c0 + u;
         const long long off = i < a.n3 ? noff[i] : -1;
-        if (off >= 0) Z[off * n_vec + col] += (d[u] + __ldg(a.b2 + i)) * s * nw[i];
+        zold[u] = off >= 0 ? Z[off * n_vec + col] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const int i = c0 + u;
+        const long long off = i < a.n3 ? noff[i] : -1;
+        if (off >= 0) Z[off * n_vec + col] = zold[u] + (d[u] + __ldg(a.b2 + i)) * s * nw[i];
       }
     }
   } else if (t == 0) {

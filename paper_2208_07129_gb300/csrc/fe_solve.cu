@@ -205,6 +205,58 @@ __global__ void __launch_bounds__(256) cg_direction_kernel_wide(T* __restrict__ 
     reinterpret_cast<V*>(p + o)[cg] = vp;
   }
 }
+// x += alpha_c p, r -= alpha_c q  (learned preconditioner: z comes from the network)
+template <typename T>
+__global__ void __launch_bounds__(256) cg_update_kernel_wide(T* __restrict__ x, T* __restrict__ r,
+                                                             const T* __restrict__ p, const T* __restrict__ q,
+                                                             const double* __restrict__ alpha, size_t n, int nv) {
+  FE_WIDE_PROLOGUE(T)
+  if (!col_ok) return;
+  T a[W::N];
+#pragma unroll
+  for (int k = 0; k < W::N; ++k) a[k] = (T)alpha[cg * W::N + k];
+  for (size_t row = r0 + threadIdx.y; row < r1; row += 8) {
+    const size_t o = row * nv;
+    V vx = reinterpret_cast<const V*>(x + o)[cg];
+    V vr = reinterpret_cast<const V*>(r + o)[cg];
+    const V vp = reinterpret_cast<const V*>(p + o)[cg];
+    const V vq = reinterpret_cast<const V*>(q + o)[cg];
+#pragma unroll
+    for (int k = 0; k < W::N; ++k) {
+      W::set(vx, k, W::get(vx, k) + a[k] * W::get(vp, k));
+      W::set(vr, k, W::get(vr, k) - a[k] * W::get(vq, k));
+    }
+    reinterpret_cast<V*>(x + o)[cg] = vx;
+    reinterpret_cast<V*>(r + o)[cg] = vr;
+  }
+}
+
+// z = dinv .* r on the columns whose r.z is not positive (descent safeguard of
+// flexible CG); other columns are left as they are and not even read.
+template <typename T>
+__global__ void __launch_bounds__(256) fcg_safeguard_kernel_wide(const T* __restrict__ r, const T* __restrict__ dinv,
+                                                                 T* __restrict__ z, const double* __restrict__ rz,
+                                                                 size_t n, int nv) {
+  FE_WIDE_PROLOGUE(T)
+  if (!col_ok) return;
+  bool bad[W::N], any = false;
+#pragma unroll
+  for (int k = 0; k < W::N; ++k) {
+    bad[k] = !(rz[cg * W::N + k] > 0.0);
+    any = any || bad[k];
+  }
+  if (!any) return;
+  for (size_t row = r0 + threadIdx.y; row < r1; row += 8) {
+    const size_t o = row * nv;
+    const V vr = reinterpret_cast<const V*>(r + o)[cg];
+    V vz = reinterpret_cast<const V*>(z + o)[cg];
+    const T d = dinv[row];
+#pragma unroll
+    for (int k = 0; k < W::N; ++k)
+      if (bad[k]) W::set(vz, k, W::get(vr, k) * d);
+    reinterpret_cast<V*>(z + o)[cg] = vz;
+  }
+}
 #undef FE_WIDE_PROLOGUE
 
 // out[c] = sum_b partial[b * nv + c]: one warp per column, lane l adds the
@@ -493,7 +545,10 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
     if ((e = col_dot<T>(p, q, n, nv, w.partial, pq, s)) != cudaSuccess) return from_cuda(e);
     cg_alpha_kernel<<<(nv + 127) / 128, 128, 0, s>>>(rz, pq, w.active, alpha, nv, c->d_status);
     if (learned) {
-      cg_update_kernel<T><<<ew_grid(tot), 256, 0, s>>>(x, r, p, q, alpha, tot, nv);
+      if (wide)
+        cg_update_kernel_wide<T><<<wide_grid(nv, Wide<T>::N), dim3(32, 8), 0, s>>>(x, r, p, q, alpha, n, nv);
+      else
+        cg_update_kernel<T><<<ew_grid(tot), 256, 0, s>>>(x, r, p, q, alpha, tot, nv);
       st = learned_precond_apply(c, r, z, nv, sizeof(T) == 8, s);
       if (st != FE_OK) return st;
       if ((e = col_dot<T>(r, z, n, nv, w.partial, rznew, s)) != cudaSuccess) return from_cuda(e);
@@ -509,7 +564,10 @@ fe_status pcg(fe_ctx* c, const T* b, T* x, int nv, const double* tol_host, int m
       }
     }
     if (learned) {
-      fcg_safeguard_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv_all, z, rznew, tot, nv);
+      if (wide)
+        fcg_safeguard_kernel_wide<T><<<wide_grid(nv, Wide<T>::N), dim3(32, 8), 0, s>>>(r, dinv_all, z, rznew, n, nv);
+      else
+        fcg_safeguard_kernel<T><<<ew_grid(tot), 256, 0, s>>>(r, dinv_all, z, rznew, tot, nv);
       if ((e = col_dot<T>(r, z, n, nv, w.partial, rznew, s)) != cudaSuccess) return from_cuda(e);
       // flexible CG (Notay): beta = -(z_new . A p) / (p . A p)
       if ((e = col_dot<T>(z, q, n, nv, w.partial, rzmid, s)) != cudaSuccess) return from_cuda(e);

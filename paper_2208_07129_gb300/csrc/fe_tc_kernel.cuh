@@ -313,15 +313,20 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
     // pass index s = 0..5, mbarrier phase = s & 1 (six completions per task).
     // Every thread's writes of the A operand become visible to the tensor
     // cores, the slot's thread 0 issues the pass, the slot waits for its
-    // completion (bounded; a timeout anywhere ends the slot's loop).  The pass
+    // completion (bounded by time; a timeout ends the slot's loop).  The pass
     // reads A from shared memory and writes D to tensor memory only, so the
     // next A may overwrite this one as soon as the pass is complete.
+    // Only the slot's first warp polls the mbarrier; the other three sleep
+    // in the named barrier that follows.
 #define FE_TC_ISSUE(S, ABUF)                                                   \
   fence_async_smem();                                                          \
   tc_fence_before();                                                           \
   slot_sync(bar);                                                              \
   if (lt == 0) tc_issue<SH, S>(tmem, ABUF, Bs, mbar);                          \
-  if (slot_sync_or(bar, !mbar_wait(mbar, (S) & 1))) { fail = true; break; }    \
+  if (slot_sync_or(bar, lt < 32 && !mbar_wait_timed(mbar, (S) & 1))) {         \
+    fail = true;                                                               \
+    break;                                                                     \
+  }                                                                            \
   tc_fence_after();
 
     FE_TC_ISSUE(0, Sb)
@@ -354,22 +359,22 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
         g00 = __ldg(cg); g01 = __ldg(cg + 1); g02 = __ldg(cg + 2);
         g11 = __ldg(cg + 3); g12 = __ldg(cg + 4); g22 = __ldg(cg + 5);
       }
+      const int nq2 = nq * nq;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int q2 = G * b + g;
         float* dl = d + g * 4 * E;   // [val | dz | dy | dx] along q3, becomes [hv | hz | hy | hx]
-        float cv[E];
+        // points (q1, q2, q3) of this line: q3 < nq exist when the line does
+        const bool line = q1 < nq && q2 < nq;
+        const float* pc = geo.ptC + (size_t)e * nq3 + q1 + nq * q2;
+        const float* pg0 = GEN ? geo.ptG + (size_t)e * 6 * nq3 + q1 + nq * q2 : nullptr;
 #pragma unroll
         for (int q3 = 0; q3 < E; ++q3) {
-          const bool ok = q1 < nq && q2 < nq && q3 < nq;
-          cv[q3] = ok ? __ldg(geo.ptC + (size_t)e * nq3 + q1 + nq * (q2 + nq * q3)) : 0.f;
-        }
-#pragma unroll
-        for (int q3 = 0; q3 < E; ++q3) {
-          float hx = 0.f, hy = 0.f, hz = 0.f;
-          if (q1 < nq && q2 < nq && q3 < nq) {
+          float hx = 0.f, hy = 0.f, hz = 0.f, cv = 0.f;
+          if (line && q3 < nq) {
+            cv = __ldg(pc + q3 * nq2);
             if (GEN) {
-              const float* pg = geo.ptG + (size_t)e * 6 * nq3 + q1 + nq * (q2 + nq * q3);
+              const float* pg = pg0 + q3 * nq2;
               g00 = __ldg(pg); g01 = __ldg(pg + nq3); g02 = __ldg(pg + 2 * nq3);
               g11 = __ldg(pg + 3 * nq3); g12 = __ldg(pg + 4 * nq3); g22 = __ldg(pg + 5 * nq3);
             }
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
             hy = g01 * dx + g11 * dy + g12 * dz;
             hz = g02 * dx + g12 * dy + g22 * dz;
           }
-          dl[q3] = cv[q3] * dl[q3];
+          dl[q3] = cv * dl[q3];
           dl[E + q3] = hz;
           dl[2 * E + q3] = hy;
           dl[3 * E + q3] = hx;
@@ -446,8 +451,8 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
   if (fail && lt == 0) {
     atomicMax(args.status, (int)FE_ETIMEOUT);
     // let any MMA of this slot still in flight finish before the tensor memory is released
-    mbar_wait(mbar, 0, 1 << 20);
-    mbar_wait(mbar, 1, 1 << 20);
+    mbar_wait_timed(mbar, 0, 100000000ull);
+    mbar_wait_timed(mbar, 1, 100000000ull);
   }
   tc_fence_before();
   __syncthreads();
