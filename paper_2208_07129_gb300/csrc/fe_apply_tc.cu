@@ -103,7 +103,7 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const Geom<float> geo = make_geom<float>(c);
-  const TcArgs a{img, c->np, c->nq, c->d_status};
+  TcArgs a{img, nullptr, c->np, c->nq, c->d_status};
   const int n_vb = (n_vec + kTcVectors - 1) / kTcVectors;
   for (int k = 0; k < c->colors.n_colors; ++k) {
     const int n = c->colors.offset[k + 1] - c->colors.offset[k];
@@ -111,6 +111,7 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
     const long long tasks = (long long)n * n_vb;
     if (tasks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>((tasks + SH::SLOTS - 1) / SH::SLOTS, (long long)sms);
+    a.cmask = c->d_tcmask + c->colors.offset[k];
     kern<<<grid, 128 * SH::SLOTS, smem, s>>>(a, c->mdev, geo, c->d_cells + c->colors.offset[k], (int)tasks, n_vec,
                                               n_vb, X, Y);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -120,17 +121,48 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
 
 }  // namespace
 
+// Per cell, in colour order: bits 0-7 / 16-23 / 32-39 mark the nodes along
+// x / y / z that exist (index < n_p) and are not Dirichlet nodes, bits 8-15 /
+// 24-31 / 40-47 those whose first writer (in colour order) the cell is, by
+// the same rules as the cell kernels' assembly.
+static std::vector<unsigned long long> tc_cell_masks(const fe_ctx* c) {
+  const MeshDev& m = c->mdev;
+  const int P = c->p, np = c->np;
+  std::vector<unsigned long long> out(c->n_cells);
+  for (size_t k = 0; k < c->n_cells; ++k) {
+    const int e = c->cells_by_color[k];
+    const int cc[3] = {e % m.nx, (e / m.nx) % m.ny, e / (m.nx * m.ny)};
+    const int n[3] = {m.nx, m.ny, m.nz}, N[3] = {m.Nx, m.Ny, m.Nz};
+    const int odd[3] = {m.last_odd_x, m.last_odd_y, m.last_odd_z};
+    unsigned long long w = 0;
+    for (int d = 0; d < 3; ++d)
+      for (int i = 0; i < np; ++i) {
+        const int g = node_coord(cc[d], i, P, N[d], m.periodic);
+        if (!on_boundary(g, N[d], m.periodic)) w |= 1ull << (16 * d + i);
+        if (first_along(cc[d], n[d], i, P, m.periodic, odd[d])) w |= 1ull << (16 * d + 8 + i);
+      }
+    out[k] = w;
+  }
+  return out;
+}
+
 cudaError_t build_tc_images(fe_ctx* c) {
   if (c->refined || c->np > 8 || c->nq > 8) return cudaSuccess;   // no tcgen05 kernel for this shape
   const std::vector<unsigned char> t = tc_image<Shape8TF32>(c), b = tc_image<Shape8BF16>(c);
-  cudaError_t e = cudaMalloc(&c->d_tcimg[0], t.size());
+  const std::vector<unsigned long long> masks = tc_cell_masks(c);
+  cudaError_t e = cudaMalloc(&c->d_tcmask, masks.size() * sizeof(unsigned long long));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_tcmask, masks.data(), masks.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_tcimg[0], t.size());
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tcimg[0], t.data(), t.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_tcimg[1], b.size());
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tcimg[1], b.data(), b.size(), cudaMemcpyHostToDevice);
   return e;
 }
 
-bool tc_supported(const fe_ctx* c) { return c->d_tcimg[0] != nullptr && c->d_tcimg[1] != nullptr; }
+bool tc_supported(const fe_ctx* c) {
+  return c->d_tcimg[0] != nullptr && c->d_tcimg[1] != nullptr && c->d_tcmask != nullptr;
+}
 
 cudaError_t apply_tc(const fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s, fe_mode mode) {
   if (!tc_supported(c)) return cudaErrorInvalidValue;

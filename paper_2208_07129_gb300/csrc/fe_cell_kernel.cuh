@@ -26,13 +26,13 @@
 
 namespace fe {
 
-__device__ __forceinline__ int dir_color(int c, int n, int last_odd) {
+__host__ __device__ __forceinline__ int dir_color(int c, int n, int last_odd) {
   return (last_odd && c == n - 1) ? 2 : (c & 1);
 }
 
 // True if cell coordinate c owns the lowest colour among the cells that share
 // the node at local index i (0..P) along one direction.
-__device__ __forceinline__ bool first_along(int c, int n, int i, int P, int periodic, int last_odd) {
+__host__ __device__ __forceinline__ bool first_along(int c, int n, int i, int P, int periodic, int last_odd) {
   const int k = dir_color(c, n, last_odd);
   if (i == 0 && (c > 0 || periodic)) {
     const int cn = c > 0 ? c - 1 : n - 1;
@@ -46,13 +46,13 @@ __device__ __forceinline__ bool first_along(int c, int n, int i, int P, int peri
 }
 
 // Global node coordinate along one direction (wrap-around when periodic).
-__device__ __forceinline__ int node_coord(int c, int i, int P, int N, int periodic) {
+__host__ __device__ __forceinline__ int node_coord(int c, int i, int P, int N, int periodic) {
   int g = c * P + i;
   if (periodic && g >= N) g -= N;
   return g;
 }
 
-__device__ __forceinline__ bool on_boundary(int g, int N, int periodic) {
+__host__ __device__ __forceinline__ bool on_boundary(int g, int N, int periodic) {
   return !periodic && (g == 0 || g == N - 1);
 }
 

@@ -15,6 +15,8 @@
 // tables of M^T, which has the same symmetry.
 #pragma once
 
+#include <algorithm>
+
 #include "fe_cell_kernel.cuh"
 
 namespace fe {
@@ -63,7 +65,10 @@ __device__ __forceinline__ void eo_apply(const EOTab<T, NO, NI>& t, const T* in,
 // epilogue), with every 1D contraction in even-odd form.  With MAP the cell's
 // nodes come from an explicit map (see map_node) instead of the structured
 // numbering: the refined meshes with hanging nodes.
-template <typename T, int NP, int NQ, bool GEN, bool SC = false, bool MAP = false>
+// LOCAL: the cell's result is written to Y[(e n_p^3 + local node) n_vec + v]
+// (a per-cell scratch block, every local node, constrained ones included)
+// instead of being assembled into the global vector.
+template <typename T, int NP, int NQ, bool GEN, bool SC = false, bool MAP = false, bool LOCAL = false>
 __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, const MeshDev& m, const Geom<T>& geo,
                                              int e, int vb, int B, int v, int ty, int nty, int n_vec,
                                              const T* __restrict__ X, T* __restrict__ Y, T* smem,
@@ -223,6 +228,12 @@ __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, con
     for (int q = 0; q < NQ; ++q) t[q] = S0[((i3 * NP + i2) * NQ + q) * B + v];
     if (!active) continue;
     eo_apply<T, NP, NQ, 1>(tab.Nt, t, o);
+    if constexpr (LOCAL) {
+      T* w = Y + ((size_t)e * NP * NP * NP + (size_t)l * NP) * n_vec + vg;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) w[(size_t)i * n_vec] = o[i];
+      continue;
+    }
     const int gy = node_coord(cy, i2, P, m.Ny, m.periodic), gz = node_coord(cz, i3, P, m.Nz, m.periodic);
     const bool con_yz = on_boundary(gy, m.Ny, m.periodic) || on_boundary(gz, m.Nz, m.periodic);
     const bool first_yz = first_along(cy, m.ny, i2, P, m.periodic, m.last_odd_y) &&
@@ -276,6 +287,77 @@ __global__ void __launch_bounds__(256) cell_apply_eo_scaled_kernel(const EOTable
                                      reinterpret_cast<T*>(smem_raw), sc);
 }
 
+// Small meshes: every cell in one launch, results to the per-cell scratch W.
+template <typename T, int NP, int NQ, bool GEN>
+__global__ void __launch_bounds__(256) cell_apply_eo_local_kernel(const EOTables<T, NP, NQ> tab, const MeshDev m,
+                                                                  const Geom<T> geo, int n_vec, int n_vb,
+                                                                  const T* __restrict__ X, T* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cell_body_eo<T, NP, NQ, GEN, false, false, true>(tab, m, geo, blockIdx.x / n_vb, blockIdx.x % n_vb, blockDim.x,
+                                                   threadIdx.x, threadIdx.y, blockDim.y, n_vec, X, W,
+                                                   reinterpret_cast<T*>(smem_raw));
+}
+
+// The cells sharing a node along one direction (one, or two at a cell
+// boundary), as (cell coordinate, local index), ordered by the direction's
+// cell colour.
+__device__ __forceinline__ int node_cells(int g, int n, int P, int periodic, int last_odd, int* c, int* l) {
+  int k;
+  if (periodic) {
+    c[0] = g / P;
+    l[0] = g - c[0] * P;
+    k = 1;
+    if (l[0] == 0) { c[1] = c[0] > 0 ? c[0] - 1 : n - 1; l[1] = P; k = 2; }
+  } else {
+    c[0] = g / P < n - 1 ? g / P : n - 1;
+    l[0] = g - c[0] * P;
+    k = 1;
+    if (l[0] == 0 && c[0] > 0) { c[1] = c[0] - 1; l[1] = P; k = 2; }
+  }
+  if (k == 2 && dir_color(c[1], n, last_odd) < dir_color(c[0], n, last_odd)) {
+    int t = c[0]; c[0] = c[1]; c[1] = t;
+    t = l[0]; l[0] = l[1]; l[1] = t;
+  }
+  return k;
+}
+
+// Y[dof][v] = sum over the cells sharing dof of W[cell][local][v], added in
+// ascending cell colour (z colour slowest, x fastest), which is the order of
+// the colour-ordered launches: the result equals theirs bit for bit.
+// Dirichlet rows are 0.
+template <typename T, int NP>
+__global__ void assemble_local_kernel(const MeshDev m, const T* __restrict__ W, T* __restrict__ Y, size_t n_dofs,
+                                      int n_vec) {
+  constexpr int P = NP - 1, NP3 = NP * NP * NP;
+  const size_t total = n_dofs * n_vec;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t dof = idx / n_vec;
+    const int v = (int)(idx - dof * n_vec);
+    const int gx = (int)(dof % m.Nx), gy = (int)((dof / m.Nx) % m.Ny), gz = (int)(dof / ((size_t)m.Nx * m.Ny));
+    if (on_boundary(gx, m.Nx, m.periodic) || on_boundary(gy, m.Ny, m.periodic) ||
+        on_boundary(gz, m.Nz, m.periodic)) {
+      Y[idx] = T(0);
+      continue;
+    }
+    int cx[2], lx[2], cy[2], ly[2], cz[2], lz[2];
+    const int kx = node_cells(gx, m.nx, P, m.periodic, m.last_odd_x, cx, lx);
+    const int ky = node_cells(gy, m.ny, P, m.periodic, m.last_odd_y, cy, ly);
+    const int kz = node_cells(gz, m.nz, P, m.periodic, m.last_odd_z, cz, lz);
+    T acc = T(0);
+    bool first = true;
+    for (int a = 0; a < kz; ++a)
+      for (int b = 0; b < ky; ++b)
+        for (int d = 0; d < kx; ++d) {
+          const size_t e = cx[d] + (size_t)m.nx * (cy[b] + (size_t)m.ny * cz[a]);
+          const T val = W[(e * NP3 + (lz[a] * NP + ly[b]) * NP + lx[d]) * n_vec + v];
+          acc = first ? val : acc + val;
+          first = false;
+        }
+    Y[idx] = acc;
+  }
+}
+
 // Host: even-odd tables of an NO x NI row-major matrix M with symmetry S.
 template <typename T, int NO, int NI>
 void make_eotab(EOTab<T, NO, NI>& t, const double* M) {
@@ -321,6 +403,25 @@ cudaError_t launch_apply_eo(const fe_ctx* c, const T* X, T* Y, int n_vec, cudaSt
   }
   const EOTables<T, NP, NQ> tab = make_eotables<T, NP, NQ>(c);
   const Geom<T> geo = make_geom<T>(c);
+  if constexpr (!SC) {
+    // Small meshes (scratch allocated at setup): one launch over all cells
+    // (one vector per CTA, so even a few cells fill the GPU) writing each
+    // cell's result to the scratch, then one gather in colour order.
+    if (c->d_small && (size_t)n_vec * NP * NP * NP * c->n_cells * sizeof(T) <= c->small_bytes) {
+      auto lk = cell_apply_eo_local_kernel<T, NP, NQ, GEN>;
+      constexpr int lines = NQ * NQ < 64 ? 32 : 64;
+      const size_t lsm = (size_t)3 * NQ * NQ * NQ * sizeof(T);
+      cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(lk), lsm);
+      if (e != cudaSuccess) return e;
+      T* W = static_cast<T*>(c->d_small);
+      lk<<<(unsigned)(c->n_cells * (size_t)n_vec), dim3(1, lines), lsm, s>>>(tab, c->mdev, geo, n_vec, n_vec, X, W);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      const size_t tot = c->n_dofs * (size_t)n_vec;
+      assemble_local_kernel<T, NP><<<(unsigned)std::min<size_t>((tot + 255) / 256, 152 * 8), 256, 0, s>>>(
+          c->mdev, W, Y, c->n_dofs, n_vec);
+      return cudaGetLastError();
+    }
+  }
   const int n_vb = (n_vec + vb - 1) / vb;
   for (int k = 0; k < c->colors.n_colors; ++k) {
     const int n = c->colors.offset[k + 1] - c->colors.offset[k];

@@ -11,6 +11,7 @@
 namespace fe {
 
 constexpr int kMaxP = 8;
+constexpr size_t kSmallSlots = 16384;   // cells x n_p^3 of a "small" mesh (see fe_ctx::d_small)
 constexpr int kMaxNQ = kMaxP + 3;
 
 // Entries of the explicit cell -> DoF map of refined meshes: the DoF index in
@@ -161,6 +162,14 @@ struct fe_ctx {
   // B operands of the tcgen05 kernel's six passes (TF32, BF16), built at setup
   // when n_p, n_q <= 8
   unsigned char* d_tcimg[2] = {nullptr, nullptr};
+  // per cell (colour order): bit masks of its nodes along x, y, z that exist
+  // and are free, and of those it writes first (tcgen05 kernel)
+  unsigned long long* d_tcmask = nullptr;
+  // small meshes (E n_p^3 <= kSmallSlots): per-cell result scratch for up to
+  // 64 FP64 vectors, so that fe_apply runs as two launches instead of one per
+  // colour; allocated at setup
+  void* d_small = nullptr;
+  size_t small_bytes = 0;
 };
 
 namespace fe {

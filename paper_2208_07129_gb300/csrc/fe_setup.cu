@@ -380,6 +380,10 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
     err = upload_point_coeff(c, zero);
   }
   if (err == cudaSuccess) err = build_tc_images(c);
+  if (err == cudaSuccess && E * (size_t)c->np * c->np * c->np <= kSmallSlots) {
+    c->small_bytes = E * (size_t)c->np * c->np * c->np * 64 * sizeof(double);
+    err = cudaMalloc(&c->d_small, c->small_bytes);
+  }
   if (err != cudaSuccess) { fe_destroy(c); return from_cuda(err); }
   *out = c;
   return FE_OK;
@@ -391,7 +395,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->d_cellG32); cudaFree(c->d_ptG32); cudaFree(c->d_ptC32); cudaFree(c->d_detJ);
   cudaFree(c->d_cellGff); cudaFree(c->d_ptGff); cudaFree(c->d_ptCff);
   cudaFree(c->d_status); cudaFree(c->d_stage);
-  cudaFree(c->d_tcimg[0]); cudaFree(c->d_tcimg[1]);
+  cudaFree(c->d_tcimg[0]); cudaFree(c->d_tcimg[1]); cudaFree(c->d_tcmask); cudaFree(c->d_small);
   if (c->copy_in) cudaStreamDestroy(c->copy_in);
   if (c->copy_out) cudaStreamDestroy(c->copy_out);
   for (cudaEvent_t ev : {c->ev_start, c->ev_in[0], c->ev_in[1], c->ev_comp[0], c->ev_comp[1], c->ev_out[0], c->ev_out[1]})

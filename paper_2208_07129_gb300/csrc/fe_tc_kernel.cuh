@@ -122,6 +122,7 @@ __device__ __forceinline__ void tc_store(TIO* p, float v) {
 
 struct TcArgs {
   const unsigned char* bimg;   // B operands of the six passes (device, core layout)
+  const unsigned long long* cmask;   // per cell of the launch: node masks (see tc_cell_masks)
   int np, nq;
   int* status;                 // FE_ETIMEOUT is raised here when a bounded wait gives up
 };
@@ -262,27 +263,24 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
     // with b = (lt / 8) % H fixed and slow = (16 j + lt / 8) / H; vector v.
     const int v = lt & 7, bq = (lt >> 3) % H;
     const bool vok = v0 + v < n_vec;
-    // Per-task node tables along x (all E entries) and along the thread's
-    // G lines in y: offsets in elements, and bit masks of the nodes that
-    // exist and are free (valid) and of those this cell writes first.
+    // Per-task node tables: offsets in elements along x (all E entries) and
+    // along the thread's G lines in y; validity and first-writer bit masks
+    // precomputed per cell on the host.
+    const unsigned long long cm = __ldg(args.cmask + task / n_vb);
+    const unsigned xv = (unsigned)(cm & 0xffu), xf = (unsigned)((cm >> 8) & 0xffu);
+    const unsigned yv_all = (unsigned)((cm >> 16) & 0xffu), yf_all = (unsigned)((cm >> 24) & 0xffu);
+    const unsigned zv_all = (unsigned)((cm >> 32) & 0xffu), zf_all = (unsigned)((cm >> 40) & 0xffu);
     int xo[E];
-    unsigned xv = 0, xf = 0;
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int gx = node_coord(cx, i, P, m.Nx, m.periodic);
-      xo[i] = gx * n_vec;
-      if (i < np && !on_boundary(gx, m.Nx, m.periodic)) xv |= 1u << i;
-      if (i < np && first_along(cx, m.nx, i, P, m.periodic, m.last_odd_x)) xf |= 1u << i;
-    }
+    for (int i = 0; i < E; ++i) xo[i] = node_coord(cx, i, P, m.Nx, m.periodic) * n_vec;
     int yo[G];
     unsigned yv = 0, yf = 0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int i2 = G * bq + g;
-      const int gy = node_coord(cy, i2, P, m.Ny, m.periodic);
-      yo[g] = gy * m.Nx * n_vec;
-      if (i2 < np && !on_boundary(gy, m.Ny, m.periodic)) yv |= 1u << g;
-      if (i2 < np && first_along(cy, m.ny, i2, P, m.periodic, m.last_odd_y)) yf |= 1u << g;
+      yo[g] = node_coord(cy, i2, P, m.Ny, m.periodic) * m.Nx * n_vec;
+      yv |= ((yv_all >> i2) & 1u) << g;
+      yf |= ((yf_all >> i2) & 1u) << g;
     }
     const size_t plane = (size_t)m.Nx * m.Ny * n_vec;
 
@@ -294,7 +292,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       if (L >= SH::LINES) continue;
       const int i3 = L / H;
       const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
-      const bool zok = vok && i3 < np && !on_boundary(gz, m.Nz, m.periodic);
+      const bool zok = vok && ((zv_all >> i3) & 1u);
       const TIO* xz = X + (size_t)gz * plane + v0 + v;
       float vals[SH::Kr(0)];
 #pragma unroll
@@ -417,8 +415,8 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       const int i3 = L / H;
       if (i3 >= np) continue;
       const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
-      const bool zcon = on_boundary(gz, m.Nz, m.periodic);
-      const bool zfirst = first_along(cz, m.nz, i3, P, m.periodic, m.last_odd_z);
+      const bool zcon = !((zv_all >> i3) & 1u);
+      const bool zfirst = (zf_all >> i3) & 1u;
       TIO* yz = Y + (size_t)gz * plane + v0 + v;
       // every read of Y (the partial sums of earlier colours) is issued
       // before the first store, so the loads overlap

@@ -228,3 +228,31 @@ def test_full_size_sampled_rows(fe, name, mode):
         print(f"{name} {mode} rel {rel:.3e}")
     finally:
         fe.fe_destroy(ctx)
+
+
+@pytest.mark.parametrize("mode,case", [("fp64", (4, 4, 4, 4, 6, False)), ("fp64", (3, 2, 3, 6, 8, True)),
+                                       ("fp32", (4, 4, 4, 4, 6, False)), ("fp64", (2, 3, 2, 3, 5, False))])
+def test_small_mesh_path_bitwise(fe, mode, case):
+    """Small meshes run as one launch over all cells into a per-cell scratch
+    plus one gather that adds each node's cell contributions in colour order;
+    the result must equal the colour-ordered launches bit for bit.  Blocks
+    wider than the scratch (65 FP64 / 129 FP32 columns) take the colour
+    path, so the same columns are compared across the two paths."""
+    nx, ny, nz, p, nq, periodic = case
+    ctx, mesh, Vo = _setup_pair(fe, nx, ny, nz, p, nq, periodic)
+    try:
+        fe.fe_set_mode(ctx, mode)
+        wide = 65 if mode == "fp64" else 129
+        dt = torch.float64 if mode == "fp64" else torch.float32
+        X = torch.from_numpy(inputs.random_block(fe.fe_num_dofs(ctx), wide, "uniform", 21)).to(device="cuda", dtype=dt)
+        Yw = torch.full_like(X, float("nan"))
+        fe.fe_apply(ctx, X, Yw)                       # colour-ordered launches
+        Xs = X[:, :wide - 1].contiguous()
+        Ys = torch.full_like(Xs, float("nan"))
+        fe.fe_apply(ctx, Xs, Ys)                      # small-mesh path
+        torch.cuda.synchronize()
+        assert torch.equal(Ys, Yw[:, :wide - 1])
+        Yref = orc.apply(mesh, p, nq, Xs.double().cpu().numpy(), Vq=Vo)
+        _compare(Ys.double().cpu().numpy(), Yref, TOL[mode])
+    finally:
+        fe.fe_destroy(ctx)
