@@ -115,6 +115,32 @@ inline bool wide_ok(int nv, const void* const* ptrs, int n_ptrs) {
   const size_t r0 = (size_t)blockIdx.x * rows_per;                                     \
   const size_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
 
+// Per-thread column sums of products.  FP64 blocks accumulate in FP64.  FP32
+// blocks accumulate in FP32 with Kahan's compensation (the running error is
+// fed back into the next term, so the sum is accurate to a few FP32 ulps
+// whatever its length) and are converted to FP64 once, for the cross-thread
+// reduction: GB300 runs FP64 at 1/64 of the FP32 rate, and two conversions
+// plus an FP64 multiply-add per element would bound these streaming kernels.
+template <typename T>
+struct ColAcc;
+template <>
+struct ColAcc<double> {
+  double s = 0.0;
+  __device__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ double value() const { return s; }
+};
+template <>
+struct ColAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ void add(float a, float b) {
+    const float y = __fsub_rn(__fmul_rn(a, b), c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ double value() const { return (double)s - (double)c; }
+};
+
 // partial[b][c] over columns c of the thread's group
 template <typename T>
 __device__ __forceinline__ void wide_store_partials(double (&s)[Wide<T>::N], bool col_ok, int cg, int nv,
@@ -137,15 +163,18 @@ template <typename T>
 __global__ void __launch_bounds__(256) col_dot_partial_wide(const T* __restrict__ a, const T* __restrict__ b,
                                                             size_t n, int nv, double* __restrict__ partial) {
   FE_WIDE_PROLOGUE(T)
-  double s[W::N] = {};
+  ColAcc<T> acc[W::N];
   if (col_ok) {
     for (size_t r = r0 + threadIdx.y; r < r1; r += 8) {
       const V va = reinterpret_cast<const V*>(a + r * nv)[cg];
       const V vb = reinterpret_cast<const V*>(b + r * nv)[cg];
 #pragma unroll
-      for (int k = 0; k < W::N; ++k) s[k] += (double)W::get(va, k) * (double)W::get(vb, k);
+      for (int k = 0; k < W::N; ++k) acc[k].add(W::get(va, k), W::get(vb, k));
     }
   }
+  double s[W::N];
+#pragma unroll
+  for (int k = 0; k < W::N; ++k) s[k] = acc[k].value();
   wide_store_partials<T>(s, col_ok, cg, nv, partial);
 }
 
@@ -157,7 +186,7 @@ __global__ void __launch_bounds__(256) cg_step_kernel_wide(T* __restrict__ x, T*
                                                            const double* __restrict__ alpha, size_t n, int nv,
                                                            double* __restrict__ partial) {
   FE_WIDE_PROLOGUE(T)
-  double s[W::N] = {};
+  ColAcc<T> acc[W::N];
   if (col_ok) {
     T a[W::N];
 #pragma unroll
@@ -177,13 +206,16 @@ __global__ void __launch_bounds__(256) cg_step_kernel_wide(T* __restrict__ x, T*
         W::set(vr, k, rn);
         const T zn = rn * d;
         W::set(vz, k, zn);
-        s[k] += (double)rn * (double)zn;
+        acc[k].add(rn, zn);
       }
       reinterpret_cast<V*>(x + o)[cg] = vx;
       reinterpret_cast<V*>(r + o)[cg] = vr;
       reinterpret_cast<V*>(z + o)[cg] = vz;
     }
   }
+  double s[W::N];
+#pragma unroll
+  for (int k = 0; k < W::N; ++k) s[k] = acc[k].value();
   wide_store_partials<T>(s, col_ok, cg, nv, partial);
 }
 
