@@ -808,7 +808,9 @@ def main():
                      "peak_source": f"152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_max:.0f} MHz; HBM {hbm} GB/s {peak_src}"},
         "modes": modes,
         "e2e": {"value": total_units / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": units * 8,
-                "d2h_bytes_per_step": units * 8},
+                "d2h_bytes_per_step": units * 8, "ms_per_step": e2e_s * 1e3,
+                "path": "fe_apply_host with pinned host buffers: the FP64 cell kernels read X and write Y "
+                        "in host memory over NVLink-C2C, no staging copies"},
         "gpu_launches": n_colors * args.steps,
         "clocks": clocks,
     }

@@ -190,9 +190,13 @@ fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream)
 fe_status fe_set_tile(fe_ctx* ctx, fe_mode mode, int vectors_per_cta, int lines, int variant);
 
 /* Same product with HOST buffers (num_dofs x n_vec, DoF-major, in the
- * context's element type): copies X_host to library-owned device staging
- * memory, applies, copies the result to Y_host and synchronises `stream`
- * before returning.  A block of at least two 128-byte column chunks (32 FP64
+ * context's element type); synchronises `stream` before returning.
+ * FE_FP64 with both buffers page-locked and device-mapped (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory): the cell kernels read X_host and write
+ * Y_host in place over the host link (NVLink-C2C on GB300); the FP64
+ * product's arithmetic hides the link traffic, so no staging copy is made.
+ * Otherwise: copies X_host to library-owned device staging
+ * memory, applies, copies the result to Y_host.  A block of at least two 128-byte column chunks (32 FP64
  * or 64 FP32 vectors) is pipelined: chunks of 16 (FP64) or 32 (FP32) columns
  * are copied in and out by strided copies on two library-owned streams while
  * the previous chunk is applied on `stream`, so the link transfers hide under

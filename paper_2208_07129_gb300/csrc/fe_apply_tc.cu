@@ -12,7 +12,7 @@ namespace fe {
 
 namespace {
 
-using Shape8TF32 = TcShape<8, 1, kTcTF32>;
+using Shape8TF32 = TcShape<8, 2, kTcTF32>;
 using Shape8BF16 = TcShape<8, 2, kTcBF16>;
 
 // Entry (n', k') of the per-line B matrix of pass s: rows n' are outputs,
@@ -170,8 +170,8 @@ cudaError_t apply_tc(const fe_ctx* c, const void* X, void* Y, int n_vec, cudaStr
   if (mode == FE_TF32) {
     const float* x = static_cast<const float*>(X);
     float* y = static_cast<float*>(Y);
-    return gen ? launch_tc<8, 1, kTcTF32, float, true>(c, c->d_tcimg[0], x, y, n_vec, s)
-               : launch_tc<8, 1, kTcTF32, float, false>(c, c->d_tcimg[0], x, y, n_vec, s);
+    return gen ? launch_tc<8, 2, kTcTF32, float, true>(c, c->d_tcimg[0], x, y, n_vec, s)
+               : launch_tc<8, 2, kTcTF32, float, false>(c, c->d_tcimg[0], x, y, n_vec, s);
   }
   if (mode == FE_BF16) {
     const float* x = static_cast<const float*>(X);

@@ -31,7 +31,7 @@
 // quadrature-point quantities of its lines and applies the point operation
 // without any exchange.
 //
-// Operands: TF32 (kind::tf32, G = 1) or BF16 (kind::f16, G = 2), both rounded
+// Operands: TF32 (kind::tf32) or BF16 (kind::f16), G = 2, both rounded
 // to nearest from FP32; the quadrature-point operation is FP32.  Storage of X
 // and Y: FP32 or BF16.  Assembly: colour-ordered, the first writer of a node
 // stores and later colours add, as in the CUDA-core kernels.
@@ -62,7 +62,7 @@ struct TcShape {
   static constexpr int LINES = E * H;                         // line groups per pass
   static constexpr int ROWS = LINES * kTcVectors;
   static constexpr int T = (ROWS + 127) / 128;                // M = 128 tiles per pass
-  static_assert(E % G == 0 && G * ES == 4, "a packed store holds G operands in 4 bytes");
+  static_assert(E % G == 0 && (G * ES == 4 || G * ES == 8), "a packed store holds the G operands of a word");
   static_assert(16 % H == 0, "a thread's line-group index b is the same in every tile");
   __host__ __device__ static constexpr int Kr(int s) { return tc_round_up(G * tc_kline(s) * E, KI); }
   __host__ __device__ static constexpr int Nr(int s) { return tc_round_up(G * tc_nline(s) * E, 16); }
@@ -151,10 +151,14 @@ __device__ __forceinline__ void tc_write_transposed(const float* d, int a, int b
     for (int q = 0; q < NQT; ++q) {
       const int off = SLOWN ? n * H * RB + q * (E / KC) * 128
                             : (n / G) * RB + ((n % G) * NL / KC) * 128 + q * (E / KC) * 128;
-      uint32_t w;
-      if constexpr (G == 1) w = tc_pack1<SH::KIND>(d[q * E + n]);
-      else w = tc_pack2<SH::KIND>(d[q * E + n], d[NL + q * E + n]);
-      *reinterpret_cast<uint32_t*>(p + off) = w;
+      if constexpr (G * ES == 8) {   // two TF32 operands: one 8-byte store
+        *reinterpret_cast<uint2*>(p + off) = make_uint2(tf32_rna(d[q * E + n]), tf32_rna(d[NL + q * E + n]));
+      } else {
+        uint32_t w;
+        if constexpr (G == 1) w = tc_pack1<SH::KIND>(d[q * E + n]);
+        else w = tc_pack2<SH::KIND>(d[q * E + n], d[NL + q * E + n]);
+        *reinterpret_cast<uint32_t*>(p + off) = w;
+      }
     }
   }
 }

@@ -159,18 +159,22 @@ def test_host_buffer_apply(fe):
         fe.fe_destroy(ctx)
 
 
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
 @pytest.mark.parametrize("mode,n_vec", [("fp64", 37), ("fp32", 70), ("tf32", 64), ("tf32x3", 33), ("df64", 40)])
-def test_host_buffer_apply_pipelined(fe, mode, n_vec):
+def test_host_buffer_apply_pipelined(fe, mode, n_vec, pinned):
     """Blocks of at least two 128-byte chunks go through the copy/compute
-    pipeline (ragged last chunk here); every column must equal the device
-    product of the whole block bit for bit."""
+    pipeline (ragged last chunk here), except FP64 on pinned buffers, which
+    is applied in place over the host link; every column must equal the
+    device product of the whole block bit for bit."""
     ctx, mesh, Vo = _setup_pair(fe, 3, 2, 3, 4, 6)
     try:
         fe.fe_set_mode(ctx, mode)
         dt = torch.float64 if mode in ("fp64", "df64") else torch.float32
         X = torch.from_numpy(inputs.random_block(fe.fe_num_dofs(ctx), n_vec, "uniform", 5)).to(dt)
-        Xh = X.pin_memory()
-        Yh = torch.full_like(Xh, float("nan")).pin_memory()
+        Xh = X.pin_memory() if pinned else X.clone()
+        Yh = torch.full_like(Xh, float("nan"))
+        if pinned:
+            Yh = Yh.pin_memory()
         for _ in range(2):            # second call reuses the stage and the streams
             fe.fe_apply_host(ctx, Xh, Yh)
         Xd = X.cuda()
