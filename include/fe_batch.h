@@ -29,7 +29,8 @@ typedef struct {
   int grid;             /* persistent CTAs */
   long long smem_bytes; /* dynamic shared memory per CTA */
   float autotune_ms;    /* device time spent timing candidate tiles */
-  int device_status;    /* FE_ETIMEOUT if a bounded wait gave up during an apply, else 0 */
+  int device_status;    /* FE_ETIMEOUT if a bounded wait gave up during an apply since
+                           the last fe_batch_stats, else 0 (cleared by the read) */
 } fe_batch_info;
 
 /* Plan a batch over n contexts (each a degree 3..8 operator with n_q = p + 2
@@ -53,8 +54,24 @@ fe_status fe_batch_create(fe_ctx* const* ctxs, int n, const int* n_vec, fe_mode 
 fe_status fe_batch_apply(fe_batch* b, const void* const* X, void* const* Y, void* stream);
 
 /* Plan statistics; vectors_per_cta / cells_per_item (optional, n entries)
- * receive each problem's tile.  Synchronous. */
+ * receive each problem's tile.  Synchronises the device, then reads and
+ * clears the batch's device status word.  Synchronous. */
 fe_status fe_batch_stats(const fe_batch* b, fe_batch_info* info, int* vectors_per_cta, int* cells_per_item);
+
+/* Limit of every bounded wait of the batch kernels (an item of colour k
+ * waiting for its problem's colour k-1 items), in seconds (default 10).  A
+ * wait that runs out records FE_ETIMEOUT in the device status word
+ * (fe_batch_stats) and lets its item proceed, so the launch always ends and
+ * the context stays usable; the results of that apply are then not valid.
+ * Takes effect from the next fe_batch_apply.  Synchronous. */
+fe_status fe_batch_set_wait_limit(fe_batch* b, double seconds);
+
+/* For exercising the bounded waits (fault injection on the host, no device
+ * fault): hold != 0 makes the items of colour color + 1 of problem `problem`
+ * wait for a completion count that colour `color` never reaches, so each of
+ * those waits runs out; hold = 0 restores the true count.  FE_EINVAL when
+ * the problem has no item of colour `color`.  Synchronous. */
+fe_status fe_batch_hold_color(fe_batch* b, int problem, int color, int hold);
 
 void fe_batch_destroy(fe_batch* b);
 

@@ -77,6 +77,12 @@ __device__ __forceinline__ void run_item(const BatchProblemDev<T>& P, const Work
   }
 }
 
+__device__ __forceinline__ unsigned long long batch_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // One persistent kernel per degree (the problems of that degree, their own
 // queue): each instantiation gets the registers its cell body needs instead
 // of those of the largest degree in the batch, and the degree's 1D tables
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const EOTables<T, 
                                                              const void* const* __restrict__ ptrs,
                                                              const WorkItem* __restrict__ items, int n_items,
                                                              int* next, int* done, const int* __restrict__ need,
-                                                             int* status) {
+                                                             int* status, const long long* __restrict__ wait_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
   T* smem = reinterpret_cast<T*>(smem_raw);
@@ -102,10 +108,11 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const EOTables<T, 
     const BatchProblemDev<T>& P = probs[w.problem];
     if (threadIdx.x == 0 && w.color > 0) {
       const int idx = w.problem * kMaxColors + w.color - 1;
-      long long spins = 0;
+      const long long limit = *wait_ns;
+      const long long t0 = (long long)batch_clock_ns();
       while (atomicAdd(&done[idx], 0) < need[idx]) {
         __nanosleep(128);
-        if (++spins > (1LL << 26)) {
+        if ((long long)batch_clock_ns() - t0 > limit) {
           atomicMax(status, (int)FE_ETIMEOUT);
           break;
         }
@@ -137,7 +144,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel_all(const BatchPro
                                                                  const void* const* __restrict__ ptrs,
                                                                  const WorkItem* __restrict__ items, int n_items,
                                                                  int* next, int* done, const int* __restrict__ need,
-                                                                 int* status) {
+                                                                 int* status, const long long* __restrict__ wait_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) T stab[kTabImage];
   __shared__ int s_item;
@@ -151,10 +158,11 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel_all(const BatchPro
     const BatchProblemDev<T>& P = probs[w.problem];
     if (threadIdx.x == 0 && w.color > 0) {
       const int idx = w.problem * kMaxColors + w.color - 1;
-      long long spins = 0;
+      const long long limit = *wait_ns;
+      const long long t0 = (long long)batch_clock_ns();
       while (atomicAdd(&done[idx], 0) < need[idx]) {
         __nanosleep(128);
-        if (++spins > (1LL << 26)) {
+        if ((long long)batch_clock_ns() - t0 > limit) {
           atomicMax(status, (int)FE_ETIMEOUT);
           break;
         }
@@ -195,6 +203,8 @@ struct fe_batch {
   int n_items = 0, n_phases = 0;
   int item_begin[kKinds + 1] = {0};   // items of degree kind k: [item_begin[k], item_begin[k + 1])
   int *d_next = nullptr, *d_done = nullptr, *d_need = nullptr, *d_status = nullptr;
+  std::vector<int> need;               // host copy of the completion counts items wait for
+  long long* d_wait_ns = nullptr;      // limit of one bounded wait (device, read by the kernels)
   const void** h_ptrs = nullptr;   // pinned host staging of the X / Y table
   void** d_ptrs = nullptr;
   size_t smem = 0;
@@ -306,7 +316,7 @@ cudaError_t launch_kind(fe_batch* b, int kind, int n_k, size_t smem) {
   kern<<<grid, kBatchThreads, smem, b->side[kind]>>>(tab, static_cast<const BatchProblemDev<T>*>(b->d_probs),
                                               const_cast<const void* const*>(b->d_ptrs),
                                               b->d_items + b->item_begin[kind], n_k, b->d_next + kind, b->d_done,
-                                              b->d_need, b->d_status);
+                                              b->d_need, b->d_status, b->d_wait_ns);
   return cudaGetLastError();
 }
 
@@ -401,6 +411,12 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
   if (e == cudaSuccess) e = cudaMalloc(&b->d_next, kKinds * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_wait_ns, sizeof(long long));
+  if (e == cudaSuccess) {
+    const long long ten_s = 10000000000LL;
+    e = cudaMemcpy(b->d_wait_ns, &ten_s, sizeof(long long), cudaMemcpyHostToDevice);
+  }
+  b->need = need;
   if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, 2 * n * sizeof(void*));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_ptrs, 2 * n * sizeof(void*));
   if (e != cudaSuccess) return from_cuda(e);
@@ -428,7 +444,8 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
       if (e == cudaSuccess)
         kern<<<b->grid, kBatchThreads, smem, b->cap>>>(static_cast<const BatchProblemDev<T>*>(b->d_probs),
                                                        const_cast<const void* const*>(b->d_ptrs), b->d_items,
-                                                       b->n_items, b->d_next, b->d_done, b->d_need, b->d_status);
+                                                       b->n_items, b->d_next, b->d_done, b->d_need, b->d_status,
+                                                       b->d_wait_ns);
     }
     for (int kind = 0; kind < kKinds && e == cudaSuccess && !merged; ++kind) {
       const int n_k = b->item_begin[kind + 1] - b->item_begin[kind];
@@ -517,9 +534,26 @@ extern "C" fe_status fe_batch_stats(const fe_batch* b, fe_batch_info* info, int*
     if (cells_per_item) cells_per_item[i] = b->cells_per_item[i];
   }
   int h = 0;
-  cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) !=
+                                                    cudaSuccess)
+    return FE_ECUDA;
   info->device_status = h;
+  cudaMemset(b->d_status, 0, sizeof(int));
   return FE_OK;
+}
+
+extern "C" fe_status fe_batch_set_wait_limit(fe_batch* b, double seconds) {
+  if (!b || !(seconds > 0.0) || seconds > 3600.0) return FE_EINVAL;
+  const long long ns = (long long)(seconds * 1e9);
+  return from_cuda(cudaMemcpy(b->d_wait_ns, &ns, sizeof(long long), cudaMemcpyHostToDevice));
+}
+
+extern "C" fe_status fe_batch_hold_color(fe_batch* b, int problem, int color, int hold) {
+  if (!b || problem < 0 || problem >= b->n || color < 0 || color + 1 >= kMaxColors) return FE_EINVAL;
+  const size_t idx = (size_t)problem * kMaxColors + color;
+  if (b->need[idx] == 0) return FE_EINVAL;   // no work item of that colour, nothing waits for it
+  const int v = hold ? 0x7fffffff : b->need[idx];
+  return from_cuda(cudaMemcpy(b->d_need + idx, &v, sizeof(int), cudaMemcpyHostToDevice));
 }
 
 extern "C" void fe_batch_destroy(fe_batch* b) {
@@ -533,7 +567,7 @@ extern "C" void fe_batch_destroy(fe_batch* b) {
   }
   if (b->fork) cudaEventDestroy(b->fork);
   cudaFree(b->d_probs); cudaFree(b->d_items); cudaFree(b->d_need); cudaFree(b->d_done); cudaFree(b->d_next);
-  cudaFree(b->d_status); cudaFree(b->d_ptrs);
+  cudaFree(b->d_status); cudaFree(b->d_ptrs); cudaFree(b->d_wait_ns);
   if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
   delete b;
 }

@@ -137,6 +137,8 @@ def lib() -> ctypes.CDLL:
         "fe_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(fe_batch_info), ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
         "fe_batch_destroy": (None, [_VP]),
+        "fe_batch_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_double]),
+        "fe_batch_hold_color": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "fe_precond_train": (ctypes.c_int, [_VP, ctypes.POINTER(fe_train_desc), ctypes.POINTER(fe_train_info), _VP]),
         "fe_precond_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
         "fe_precond_set_weights": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
@@ -497,6 +499,15 @@ def fe_batch_stats(batch: int, n: int) -> dict:
     d["vectors_per_cta"] = list(vb)
     d["cells_per_item"] = list(cb)
     return d
+
+
+def fe_batch_set_wait_limit(batch: int, seconds: float) -> None:
+    _check(lib().fe_batch_set_wait_limit(batch, float(seconds)), "fe_batch_set_wait_limit")
+
+
+def fe_batch_hold_color(batch: int, problem: int, color: int, hold: bool) -> None:
+    """Host-side fault injection for the bounded waits (see fe_batch.h)."""
+    _check(lib().fe_batch_hold_color(batch, problem, color, int(bool(hold))), "fe_batch_hold_color")
 
 
 def fe_batch_destroy(batch: int) -> None:

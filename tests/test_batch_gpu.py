@@ -76,3 +76,42 @@ def test_batch_rejects_unsupported(fe):
             fe.fe_batch_create([ctx], [4])            # p = 2 is outside the batch kinds
     finally:
         fe.fe_destroy(ctx)
+
+
+def test_bounded_wait_runs_out_and_recovers(fe):
+    """A colour whose completion count can never be reached (injected on the
+    host) makes the next colour's waits run out after the wait limit: the
+    launch ends, the status word reports FE_ETIMEOUT, and after the count is
+    restored the same batch gives the per-problem results again."""
+    ctxs, Xs, Ys, Yref = [], [], [], []
+    try:
+        for k, (n, p, nv, per) in enumerate([(3, 3, 5, True), (2, 4, 8, False)]):
+            w = inputs.Workload(f"t{k}", n, n, n, per, p, p + 2, nv, "normal", 60 + k, "gauss", v_seed=160 + k)
+            ctx = fe.setup_workload(w)
+            ctxs.append(ctx)
+            X = torch.from_numpy(w.make_x()).cuda()
+            Xs.append(X)
+            Ys.append(torch.empty_like(X))
+            Y = torch.empty_like(X)
+            fe.fe_apply(ctx, X, Y)
+            Yref.append(Y)
+        b = fe.fe_batch_create(ctxs, [5, 8], mode="fp64", autotune=False)
+        try:
+            fe.fe_batch_set_wait_limit(b, 0.02)
+            fe.fe_batch_hold_color(b, 0, 0, True)
+            fe.fe_batch_apply(b, Xs, Ys)
+            torch.cuda.synchronize()
+            assert fe.fe_batch_stats(b, 2)["device_status"] == fe.FE_ETIMEOUT
+            fe.fe_batch_hold_color(b, 0, 0, False)
+            fe.fe_batch_apply(b, Xs, Ys)
+            torch.cuda.synchronize()
+            assert fe.fe_batch_stats(b, 2)["device_status"] == 0
+            for Y, R in zip(Ys, Yref):
+                assert torch.equal(Y, R)
+            with pytest.raises(fe.FeError):
+                fe.fe_batch_hold_color(b, 5, 0, True)     # no such problem
+        finally:
+            fe.fe_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            fe.fe_destroy(c)
