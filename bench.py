@@ -657,6 +657,44 @@ def profile_precond(fe, torch, n: int = 12, n_vec: int = 128, reps: int = 3):
         fe.fe_destroy(ctx)
 
 
+def profile_apply(fe, torch, n: int, mode: str, n_vec: int = 64, reps: int = 2):
+    """A small case of one mode's cell kernel for hardware-counter captures:
+    n^3 periodic cells, p = 6, n_q = 8, n_vec vectors (the 32^3 workload's
+    shape), `reps` products after setup; prints the time per product."""
+    w = inputs.Workload(f"{n}^3 periodic, p=6, n_q=8, n_vec={n_vec}", n, n, n, True, 6, 8, n_vec, "normal", 2,
+                        "gauss", v_seed=12)
+    ctx = fe.setup_workload(w)
+    try:
+        fe.fe_set_mode(ctx, mode)
+        X = torch.from_numpy(w.make_x()).to(device="cuda", dtype=fe.block_dtype(ctx))
+        Y = torch.empty_like(X)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fe.fe_apply(ctx, X, Y)
+        b.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": w.name, "mode": mode, "ms_per_apply": a.elapsed_time(b) / reps}), flush=True)
+    finally:
+        fe.fe_destroy(ctx)
+
+
+def profile_solve(fe, torch, iterations: int, inner: str = "fp32"):
+    """A short block-PCG run on the 24^3, p=6, 128-column problem (inner mode
+    `inner` with FP64 refinement, capped at `iterations` inner iterations)
+    for per-kernel launch lists."""
+    w = inputs.WORKLOADS["c5"]
+    ctx = fe.setup_workload(w)
+    try:
+        B = torch.from_numpy(w.make_rhs()).cuda()
+        X = torch.zeros_like(B)
+        r = fe.fe_solve(ctx, B, X, rtol=1e-8, max_it=iterations, precond="jacobi", inner_mode=inner)
+        r.pop("rel_res", None)
+        print(json.dumps({"workload": w.name, "inner": inner, **r}), flush=True)
+    finally:
+        fe.fe_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,6 +710,9 @@ def main():
     ap.add_argument("--no-chfsi", action="store_true")
     ap.add_argument("--no-refined", action="store_true")
     ap.add_argument("--profile-precond", type=int, default=0, help="cells per direction of a preconditioner-only run")
+    ap.add_argument("--profile-apply", type=int, default=0, help="cells per direction of a one-mode apply run "
+                                                                  "(mode: the first of --modes)")
+    ap.add_argument("--profile-solve", type=int, default=0, help="inner iterations of a short 24^3 PCG run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -687,6 +728,12 @@ def main():
     fe.lib()
     if args.profile_precond:
         profile_precond(fe, torch, n=args.profile_precond)
+        return
+    if args.profile_apply:
+        profile_apply(fe, torch, args.profile_apply, args.modes.split(",")[0])
+        return
+    if args.profile_solve:
+        profile_solve(fe, torch, args.profile_solve)
         return
     peaks, peak_src = measured_peaks()
     w = inputs.WORKLOADS[args.workload]
