@@ -52,18 +52,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
 }
 
-// Bounded wait on an mbarrier phase; returns false when the limit is reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase, int limit = 1 << 24) {
-  uint32_t done = 0;
-  for (int it = 0; it < limit && !done; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(phase));
-  }
-  return done != 0;
-}
-
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
