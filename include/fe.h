@@ -165,7 +165,10 @@ fe_status fe_set_mode(fe_ctx* ctx, fe_mode mode);
 fe_mode fe_get_mode(const fe_ctx* ctx);
 
 /* Y = A X for n_vec >= 0 vectors (Algorithm 2 per cell, batched over cells and
- * vector blocks as in Algorithm 4, assembled without atomics by cell colours).
+ * vector blocks as in Algorithm 4, assembled by cell colours: no two cells of
+ * a colour share a node and colours run in order, so every node's sum is
+ * formed in a fixed order and results are deterministic; the tcgen05 kernel's
+ * TMA path zeroes Y and adds each cell's result box with a bulk reduce).
  * X, Y: device, num_dofs x n_vec, dtype of the current mode, X != Y (no
  * overlap).  Y is overwritten, never accumulated.  Asynchronous on stream.
  * On a refined mesh with hanging nodes the product first distributes X into a
@@ -183,10 +186,14 @@ fe_status fe_apply(fe_ctx* ctx, const void* X, void* Y, int n_vec, void* stream)
  * kernel; FE_FP32: 0 or 1 = line kernel, 2 = register-plane kernel, n_q <= 8
  * only, 3 = line kernel with even-odd contractions; FE_DF64: 0, the
  * double-float even-odd line kernel).
- * FE_TF32 / FE_BF16: the tile is fixed; variant 0 = tcgen05 kernel where
- * built (n_p, n_q <= 8), 1 = warp-level MMA kernel (the other arguments are
- * ignored).  FE_TF32X3 and FE_BF16S: FE_EUNSUPPORTED.  Applies to later
- * fe_apply calls. */
+ * FE_TF32 / FE_BF16 / FE_BF16S (one setting for the three): the tile is
+ * fixed; variant 0 = tcgen05 kernel where built (n_p, n_q <= 8), moving each
+ * cell's values with TMA boxes when X and Y are 16-byte aligned and a node's
+ * n_vec values fill whole 16-byte units (n_vec >= 8, a multiple of 4 for
+ * FP32 storage and of 8 for BF16 storage), else with per-thread loads and
+ * stores; 1 = warp-level MMA kernel (FE_TF32 / FE_BF16 only); 2 = tcgen05
+ * kernel with per-thread loads and stores always (the other arguments are
+ * ignored).  FE_TF32X3: FE_EUNSUPPORTED.  Applies to later fe_apply calls. */
 fe_status fe_set_tile(fe_ctx* ctx, fe_mode mode, int vectors_per_cta, int lines, int variant);
 
 /* Same product with HOST buffers (num_dofs x n_vec, DoF-major, in the

@@ -38,7 +38,7 @@ extern "C" fe_status fe_apply(fe_ctx* c, const void* X, void* Y, int n_vec, void
     case FE_FP32: e = apply_cc_f32(c, static_cast<const float*>(X), static_cast<float*>(Y), n_vec, s); break;
     case FE_TF32:
     case FE_BF16:
-      if (c->tc_variant == 0 && tc_supported(c)) {
+      if (c->tc_variant != 1 && tc_supported(c)) {
         e = apply_tc(c, X, Y, n_vec, s, c->mode);
         break;
       }

@@ -1,9 +1,12 @@
 // Host side of the tcgen05 cell kernel (fe_tc_kernel.cuh): the B operands of
-// the six passes, built once per context from the FP64 1D tables, and the
-// per-colour persistent launches.
+// the six passes, built once per context from the FP64 1D tables, the tensor
+// maps of X and Y for the TMA boxes, and the per-colour persistent launches.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "fe_dispatch.cuh"
 #include "fe_tc_kernel.cuh"
@@ -88,10 +91,46 @@ std::vector<unsigned char> tc_image(const fe_ctx* c) {
   return img;
 }
 
-template <int E, int G, int KIND, typename TIO, bool GEN>
-cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, TIO* Y, int n_vec, cudaStream_t s) {
+// cuTensorMapEncodeTiled from the driver, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a block (node-major, n_vec values per node) as the 4-D
+// tensor (vector, x, y, z) of the stored node grid, with the box of one task:
+// 8 vectors x n_p^3 nodes.  False where TMA cannot address the block: a base
+// not 16-byte aligned, or a node row (n_vec values) not a multiple of 16
+// bytes, or fewer vectors than one box row.
+bool tc_tensor_map(CUtensorMap* map, const fe_ctx* c, const void* base, int n_vec, bool bf16) {
+  const size_t es = bf16 ? 2 : 4;
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (n_vec * es) % 16 != 0 || n_vec < kTcVectors) return false;
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (fn == nullptr) return false;
+  const MeshDev& m = c->mdev;
+  const cuuint64_t dims[4] = {(cuuint64_t)n_vec, (cuuint64_t)m.Nx, (cuuint64_t)m.Ny, (cuuint64_t)m.Nz};
+  const cuuint64_t strides[3] = {(cuuint64_t)n_vec * es, (cuuint64_t)n_vec * es * m.Nx,
+                                 (cuuint64_t)n_vec * es * m.Nx * m.Ny};
+  const cuuint32_t box[4] = {(cuuint32_t)kTcVectors, (cuuint32_t)c->np, (cuuint32_t)c->np, (cuuint32_t)c->np};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base),
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int E, int G, int KIND, typename TIO, bool GEN, bool TMA, bool QF>
+cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, TIO* Y, int n_vec, cudaStream_t s,
+                      const CUtensorMap& xm, const CUtensorMap& ym) {
   using SH = TcShape<E, G, KIND>;
-  auto kern = tc_apply_kernel<E, G, KIND, TIO, GEN>;
+  auto kern = tc_apply_kernel<E, G, KIND, TIO, GEN, TMA, QF>;
   // One CTA per SM: its shared-memory request (more than half of an SM's)
   // keeps a second CTA, which would need tensor-memory columns the first
   // holds, off the SM.
@@ -102,6 +141,8 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  // the bulk reduces add every colour's result to Y
+  if (TMA && (e = cudaMemsetAsync(Y, 0, c->n_dofs * (size_t)n_vec * sizeof(TIO), s)) != cudaSuccess) return e;
   const Geom<float> geo = make_geom<float>(c);
   TcArgs a{img, nullptr, c->np, c->nq, c->d_status};
   const int n_vb = (n_vec + kTcVectors - 1) / kTcVectors;
@@ -113,10 +154,33 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
     const int grid = (int)std::min<long long>((tasks + SH::SLOTS - 1) / SH::SLOTS, (long long)sms);
     a.cmask = c->d_tcmask + c->colors.offset[k];
     kern<<<grid, 128 * SH::SLOTS, smem, s>>>(a, c->mdev, geo, c->d_cells + c->colors.offset[k], (int)tasks, n_vec,
-                                              n_vb, X, Y);
+                                              n_vb, X, Y, xm, ym);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// TMA boxes where the blocks allow them (and fe_set_tile has not chosen the
+// thread path), the n_q = 8 specialisation where it applies.
+template <int KIND, typename TIO>
+cudaError_t run_tc(const fe_ctx* c, const unsigned char* img, const void* Xv, void* Yv, int n_vec, cudaStream_t s) {
+  const TIO* X = static_cast<const TIO*>(Xv);
+  TIO* Y = static_cast<TIO*>(Yv);
+  constexpr bool bf16 = sizeof(TIO) == 2;
+  const bool gen = c->general != 0;
+  CUtensorMap xm, ym;
+  std::memset(&xm, 0, sizeof(xm));
+  std::memset(&ym, 0, sizeof(ym));
+  const bool tma = c->tc_variant != 2 && tc_tensor_map(&xm, c, X, n_vec, bf16) && tc_tensor_map(&ym, c, Y, n_vec, bf16);
+  if (tma) {
+    if (c->nq == 8)
+      return gen ? launch_tc<8, 2, KIND, TIO, true, true, true>(c, img, X, Y, n_vec, s, xm, ym)
+                 : launch_tc<8, 2, KIND, TIO, false, true, true>(c, img, X, Y, n_vec, s, xm, ym);
+    return gen ? launch_tc<8, 2, KIND, TIO, true, true, false>(c, img, X, Y, n_vec, s, xm, ym)
+               : launch_tc<8, 2, KIND, TIO, false, true, false>(c, img, X, Y, n_vec, s, xm, ym);
+  }
+  return gen ? launch_tc<8, 2, KIND, TIO, true, false, false>(c, img, X, Y, n_vec, s, xm, ym)
+             : launch_tc<8, 2, KIND, TIO, false, false, false>(c, img, X, Y, n_vec, s, xm, ym);
 }
 
 }  // namespace
@@ -166,25 +230,9 @@ bool tc_supported(const fe_ctx* c) {
 
 cudaError_t apply_tc(const fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s, fe_mode mode) {
   if (!tc_supported(c)) return cudaErrorInvalidValue;
-  const bool gen = c->general != 0;
-  if (mode == FE_TF32) {
-    const float* x = static_cast<const float*>(X);
-    float* y = static_cast<float*>(Y);
-    return gen ? launch_tc<8, 2, kTcTF32, float, true>(c, c->d_tcimg[0], x, y, n_vec, s)
-               : launch_tc<8, 2, kTcTF32, float, false>(c, c->d_tcimg[0], x, y, n_vec, s);
-  }
-  if (mode == FE_BF16) {
-    const float* x = static_cast<const float*>(X);
-    float* y = static_cast<float*>(Y);
-    return gen ? launch_tc<8, 2, kTcBF16, float, true>(c, c->d_tcimg[1], x, y, n_vec, s)
-               : launch_tc<8, 2, kTcBF16, float, false>(c, c->d_tcimg[1], x, y, n_vec, s);
-  }
-  if (mode == FE_BF16S) {
-    const __nv_bfloat16* x = static_cast<const __nv_bfloat16*>(X);
-    __nv_bfloat16* y = static_cast<__nv_bfloat16*>(Y);
-    return gen ? launch_tc<8, 2, kTcBF16, __nv_bfloat16, true>(c, c->d_tcimg[1], x, y, n_vec, s)
-               : launch_tc<8, 2, kTcBF16, __nv_bfloat16, false>(c, c->d_tcimg[1], x, y, n_vec, s);
-  }
+  if (mode == FE_TF32) return run_tc<kTcTF32, float>(c, c->d_tcimg[0], X, Y, n_vec, s);
+  if (mode == FE_BF16) return run_tc<kTcBF16, float>(c, c->d_tcimg[1], X, Y, n_vec, s);
+  if (mode == FE_BF16S) return run_tc<kTcBF16, __nv_bfloat16>(c, c->d_tcimg[1], X, Y, n_vec, s);
   return cudaErrorInvalidValue;
 }
 

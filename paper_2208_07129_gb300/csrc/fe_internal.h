@@ -158,7 +158,8 @@ struct fe_ctx {
   int vb64 = 8, nty64 = 16, vb32 = 8, nty32 = 32, vbdf = 8, ntydf = 32;
   int fp32_variant = 0;   // 0 / 1: line kernel, 2: register-plane kernel, 3: even-odd line kernel
   int fp64_variant = 0;   // 0: even-odd line kernel, 1: plain line kernel
-  int tc_variant = 0;     // FE_TF32 / FE_BF16: 0 tcgen05 kernel (where built), 1 warp-MMA kernel
+  int tc_variant = 0;     // FE_TF32 / FE_BF16 / FE_BF16S: 0 tcgen05 kernel (where built) with TMA boxes where
+                          // the blocks allow, 1 warp-MMA kernel (not FE_BF16S), 2 tcgen05 with thread loads/stores
   // B operands of the tcgen05 kernel's six passes (TF32, BF16), built at setup
   // when n_p, n_q <= 8
   unsigned char* d_tcimg[2] = {nullptr, nullptr};

@@ -497,7 +497,10 @@ extern "C" fe_status fe_set_tile(fe_ctx* c, fe_mode mode, int vectors_per_cta, i
     c->nty32 = lines;
     c->fp32_variant = variant;
   } else if (mode == FE_TF32 || mode == FE_BF16) {
-    if (variant > 1) return FE_EINVAL;   // tensor-core tiles are fixed: only the kernel is chosen
+    if (variant > 2) return FE_EINVAL;   // tensor-core tiles are fixed: only the kernel is chosen
+    c->tc_variant = variant;
+  } else if (mode == FE_BF16S) {
+    if (variant != 0 && variant != 2) return FE_EINVAL;   // tcgen05 only
     c->tc_variant = variant;
   } else {
     return FE_EUNSUPPORTED;

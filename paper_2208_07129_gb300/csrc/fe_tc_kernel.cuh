@@ -33,13 +33,15 @@
 //
 // Operands: TF32 (kind::tf32) or BF16 (kind::f16), G = 2, both rounded
 // to nearest from FP32; the quadrature-point operation is FP32.  Storage of X
-// and Y: FP32 or BF16.  Assembly: colour-ordered, the first writer of a node
-// stores and later colours add, as in the CUDA-core kernels.
+// and Y: FP32 or BF16.  Data movement: TMA boxes of 8 vectors x n_p^3 nodes
+// in and bulk reduce-adds out where the block layout allows, else per-thread
+// loads and stores.  Assembly: colour-ordered either way (see the kernel).
 #pragma once
 
 #include <cuda_bf16.h>
 
 #include "fe_cell_kernel.cuh"
+#include "fe_tma.cuh"
 #include "fe_umma.cuh"
 
 namespace fe {
@@ -213,36 +215,89 @@ __device__ __forceinline__ bool slot_sync_or(int id, bool v) {
   return r != 0;
 }
 
+// Node rows past the n_p^3 rows of a TMA-loaded cell tile that the F-x
+// operand build reads: line groups and x indices padded to E alias later rows
+// of the tile (their B entries are zero), and the rows past its end must read
+// as zero.
+template <int E>
+__host__ __device__ constexpr int tc_guard_rows(int np) {
+  return (E - 1) * (np + 1) - np * np + 1 > 0 ? (E - 1) * (np + 1) - np * np + 1 : 0;
+}
+
+template <typename TIO>
+__device__ __forceinline__ TIO tc_zero() {
+  if constexpr (sizeof(TIO) == 4) return 0.f;
+  else return __ushort_as_bfloat16((unsigned short)0);
+}
+__device__ __forceinline__ void tc_atomic_add(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void tc_atomic_add(__nv_bfloat16* p, float v) { atomicAdd(p, __float2bfloat16_rn(v)); }
+
 // One persistent CTA per SM with SH::SLOTS task slots.  Slot s is warpgroup s
 // (threads 128 s ... 128 s + 127): it loops over the (cell, 8-vector block)
 // tasks s, s + SLOTS, ... of this CTA's share of one colour, with its own
-// tensor-memory columns, A buffers and mbarrier, so the slots' passes overlap
+// tensor-memory columns, A buffers and mbarriers, so the slots' passes overlap
 // one another's latencies.  Thread lt of a slot owns TMEM lane lt, i.e. row
 // lt of every 128-row tile of a pass.
-template <int E, int G, int KIND, typename TIO, bool GEN>
+//
+// TMA: the cell's values for the task's 8 vectors arrive as one tensor-map
+// box (8 vectors x n_p^3 nodes, dense) in the slot's A buffer; nodes that are
+// Dirichlet nodes are zeroed and nodes across a periodic seam (outside the
+// box) fetched by the threads, then every thread builds its rows of the F-x
+// operand from the box.  The result is written back into the same buffer as
+// a box of the same shape (Dirichlet nodes 0) and added to Y by one bulk
+// reduce; Y starts at zero, cells of one colour share no node, and colours
+// run in order, so every sum is formed in the same order as by the
+// colour-ordered stores and adds of the thread path.  Seam nodes are added
+// by the threads.  Without TMA (n_vec not a multiple of 16 bytes, unaligned
+// blocks, or fe_set_tile variant 2) every thread loads and stores its own
+// values, first writers storing and later colours adding.
+// QF: n_q = E, so every quadrature point of the padded lines exists.
+template <int E, int G, int KIND, typename TIO, bool GEN, bool TMA, bool QF>
 __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
     tc_apply_kernel(const TcArgs args, const MeshDev m, const Geom<float> geo, const int* __restrict__ cells,
-                    int n_tasks, int n_vec, int n_vb, const TIO* __restrict__ X, TIO* __restrict__ Y) {
+                    int n_tasks, int n_vec, int n_vb, const TIO* __restrict__ X, TIO* __restrict__ Y,
+                    const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap) {
   using SH = TcShape<E, G, KIND>;
-  constexpr int H = SH::H, T = SH::T, SLOTS = SH::SLOTS;
+  constexpr int H = SH::H, T = SH::T, SLOTS = SH::SLOTS, V = kTcVectors;
+  static_assert(!TMA || (E * E * E + 32) * V * (int)sizeof(TIO) <= SH::M_BYTES, "a cell box fits the A buffer");
+  static_assert(SH::B_BYTES % 128 == 0 && SH::SLOT_BYTES % 128 == 0 && SH::S_BYTES % 128 == 0,
+                "A buffers start 128 bytes apart");
   extern __shared__ __align__(128) unsigned char smem[];
   const int t = threadIdx.x, warp = t >> 5, slot = t >> 7, lt = t & 127;
   unsigned char* Bs = smem;
   unsigned char* Sb = smem + SH::B_BYTES + slot * SH::SLOT_BYTES;
   unsigned char* Mb = Sb + SH::S_BYTES;
   uint64_t* mbars = reinterpret_cast<uint64_t*>(smem + SH::B_BYTES + SLOTS * SH::SLOT_BYTES);
-  uint64_t* mbar = mbars + slot;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbars + SLOTS);
+  uint64_t* mbar = mbars + slot;            // MMA completions (six per task)
+  uint64_t* lbar = mbars + SLOTS + slot;    // box loads (one per task)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbars + 2 * SLOTS);
+  TIO* box = reinterpret_cast<TIO*>(Mb);
   const int bar = 1 + slot;
-  const int np = args.np, nq = args.nq, P = np - 1;
-  const int nq3 = nq * nq * nq;
+  const int np = args.np, nq = QF ? E : args.nq, P = np - 1;
+  const int nq2 = nq * nq, nq3 = nq2 * nq;
+  const int np2 = np * np, np3 = np2 * np;
+  if constexpr (TMA) {
+    // box destinations must be 128-byte aligned; the layout keeps every A
+    // buffer at a multiple of 128 bytes from the base of shared memory
+    if (smem_u32(smem) & 127u) {
+      if (t == 0) atomicMax(args.status, (int)FE_EUNSUPPORTED);
+      return;
+    }
+  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(SH::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (lt == 0) mbar_init(mbar, 1);
+  if (lt == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(lbar, 1);
+    if constexpr (TMA) {
+      tma_prefetch_map(&xmap);
+      tma_prefetch_map(&ymap);
+    }
+  }
   {  // B operands -> shared (once per CTA); the A buffers start at zero
     const uint4* src = reinterpret_cast<const uint4*>(args.bimg);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
@@ -257,7 +312,8 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
   tc_fence_after();
   const uint32_t tmem = *tslot + (uint32_t)(slot * SH::SLOT_COLS);
   const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  bool fail = false;
+  bool fail = false, load_pending = false;
+  uint32_t lphase = 0;
 
   for (int task = blockIdx.x * SLOTS + slot; task < n_tasks && !fail; task += gridDim.x * SLOTS) {
     const int e = cells[task / n_vb];
@@ -267,48 +323,117 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
     // with b = (lt / 8) % H fixed and slow = (16 j + lt / 8) / H; vector v.
     const int v = lt & 7, bq = (lt >> 3) % H;
     const bool vok = v0 + v < n_vec;
-    // Per-task node tables: offsets in elements along x (all E entries) and
-    // along the thread's G lines in y; validity and first-writer bit masks
-    // precomputed per cell on the host.
+    // Per-task node tables: validity and first-writer bit masks precomputed
+    // per cell on the host (bit i: node i along the direction).
     const unsigned long long cm = __ldg(args.cmask + task / n_vb);
     const unsigned xv = (unsigned)(cm & 0xffu), xf = (unsigned)((cm >> 8) & 0xffu);
     const unsigned yv_all = (unsigned)((cm >> 16) & 0xffu), yf_all = (unsigned)((cm >> 24) & 0xffu);
     const unsigned zv_all = (unsigned)((cm >> 32) & 0xffu), zf_all = (unsigned)((cm >> 40) & 0xffu);
-    int xo[E];
-#pragma unroll
-    for (int i = 0; i < E; ++i) xo[i] = node_coord(cx, i, P, m.Nx, m.periodic) * n_vec;
-    int yo[G];
-    unsigned yv = 0, yf = 0;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int i2 = G * bq + g;
-      yo[g] = node_coord(cy, i2, P, m.Ny, m.periodic) * m.Nx * n_vec;
-      yv |= ((yv_all >> i2) & 1u) << g;
-      yf |= ((yf_all >> i2) & 1u) << g;
-    }
     const size_t plane = (size_t)m.Nx * m.Ny * n_vec;
-
-    // ---- gather: row (i3, b) x v, lines i2 = G b + g, K = [g][i1]; every
-    // load of the thread is issued before the first use ----
+    // thread path: element offsets along x (all E entries) and along the
+    // thread's G lines in y
+    int xo[TMA ? 1 : E];
+    int yo[TMA ? 1 : G];
+    unsigned yv = 0, yf = 0;
+    // TMA path: the cell lies across a periodic seam along x / y / z; a
+    // "clean" cell has neither seam nor Dirichlet node
+    bool wx = false, wy = false, wz = false, clean = true;
+    if constexpr (!TMA) {
 #pragma unroll
-    for (int j = 0; j < T; ++j) {
-      const int r = j * 128 + lt, L = r >> 3;
-      if (L >= SH::LINES) continue;
-      const int i3 = L / H;
-      const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
-      const bool zok = vok && ((zv_all >> i3) & 1u);
-      const TIO* xz = X + (size_t)gz * plane + v0 + v;
-      float vals[SH::Kr(0)];
+      for (int i = 0; i < E; ++i) xo[i] = node_coord(cx, i, P, m.Nx, m.periodic) * n_vec;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        const bool ok = zok && ((yv >> g) & 1u);
+        const int i2 = G * bq + g;
+        yo[g] = node_coord(cy, i2, P, m.Ny, m.periodic) * m.Nx * n_vec;
+        yv |= ((yv_all >> i2) & 1u) << g;
+        yf |= ((yf_all >> i2) & 1u) << g;
+      }
+    }
+
+    if constexpr (TMA) {
+      // ---- gather: one box load, seam and Dirichlet fix-ups, operand rows ----
+      const unsigned full = (1u << np) - 1u;
+      wx = m.periodic && cx == m.nx - 1;
+      wy = m.periodic && cy == m.ny - 1;
+      wz = m.periodic && cz == m.nz - 1;
+      clean = xv == full && yv_all == full && zv_all == full && !(wx || wy || wz);
+      if (lt == 0) {
+        bulk_wait_read_all();   // the previous task's reduce has read its result box
+        mbar_arrive_expect_tx(lbar, (uint32_t)(np3 * V * (int)sizeof(TIO)));
+        tma_load_4d(box, &xmap, v0, cx * P, cy * P, cz * P, lbar);
+      }
+      {
+        const int words = tc_guard_rows<E>(np) * V * (int)sizeof(TIO) / 16;
+        uint4* gz = reinterpret_cast<uint4*>(Mb + np3 * V * (int)sizeof(TIO));
+        for (int k = lt; k < words; k += 128) gz[k] = make_uint4(0, 0, 0, 0);
+      }
+      load_pending = true;
+      if (slot_sync_or(bar, !mbar_wait_timed(lbar, lphase))) {
+        fail = true;
+        break;
+      }
+      load_pending = false;
+      lphase ^= 1u;
+      if (!clean) {   // the same for every thread of the slot
+        for (int n = lt; n < np3; n += 128) {
+          const int i1 = n % np, i2 = (n / np) % np, i3 = n / np2;
+          TIO* row = box + n * V;
+          if (!((xv >> i1) & (yv_all >> i2) & (zv_all >> i3) & 1u)) {
 #pragma unroll
-        for (int i1 = 0; i1 < E; ++i1)
-          vals[g * E + i1] = (ok && ((xv >> i1) & 1u)) ? tc_load(xz + yo[g] + xo[i1]) : 0.f;
+            for (int k = 0; k < V; ++k) row[k] = tc_zero<TIO>();
+          } else if ((wx && i1 == P) || (wy && i2 == P) || (wz && i3 == P)) {
+            const size_t node = (size_t)node_coord(cx, i1, P, m.Nx, m.periodic) +
+                                (size_t)m.Nx * (node_coord(cy, i2, P, m.Ny, m.periodic) +
+                                                (size_t)m.Ny * node_coord(cz, i3, P, m.Nz, m.periodic));
+            const TIO* src = X + node * n_vec + v0;
+#pragma unroll
+            for (int k = 0; k < V; ++k) row[k] = v0 + k < n_vec ? src[k] : tc_zero<TIO>();
+          }
+        }
+        slot_sync(bar);
       }
 #pragma unroll
-      for (int k = G * E; k < SH::Kr(0); ++k) vals[k] = 0.f;
-      tc_write_row<SH, SH::Kr(0)>(vals, r, Sb);
+      for (int j = 0; j < T; ++j) {
+        const int r = j * 128 + lt, L = r >> 3;
+        if (L >= SH::LINES) continue;
+        const int i3 = L / H;
+        float vals[SH::Kr(0)];
+#pragma unroll
+        for (int k = 0; k < SH::Kr(0); ++k) vals[k] = 0.f;
+        if (i3 < np) {
+          const TIO* s0 = box + (i3 * np + G * (L % H)) * np * V + v;
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const TIO* sg = s0 + g * np * V;
+#pragma unroll
+            for (int i1 = 0; i1 < E; ++i1) vals[g * E + i1] = tc_load(sg + i1 * V);
+          }
+        }
+        tc_write_row<SH, SH::Kr(0)>(vals, r, Sb);
+      }
+    } else {
+      // ---- gather: row (i3, b) x v, lines i2 = G b + g, K = [g][i1]; every
+      // load of the thread is issued before the first use ----
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        const int r = j * 128 + lt, L = r >> 3;
+        if (L >= SH::LINES) continue;
+        const int i3 = L / H;
+        const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
+        const bool zok = vok && ((zv_all >> i3) & 1u);
+        const TIO* xz = X + (size_t)gz * plane + v0 + v;
+        float vals[SH::Kr(0)];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const bool ok = zok && ((yv >> g) & 1u);
+#pragma unroll
+          for (int i1 = 0; i1 < E; ++i1)
+            vals[g * E + i1] = (ok && ((xv >> i1) & 1u)) ? tc_load(xz + yo[g] + xo[i1]) : 0.f;
+        }
+#pragma unroll
+        for (int k = G * E; k < SH::Kr(0); ++k) vals[k] = 0.f;
+        tc_write_row<SH, SH::Kr(0)>(vals, r, Sb);
+      }
     }
 
     // ---- the six passes ----
@@ -361,19 +486,18 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
         g00 = __ldg(cg); g01 = __ldg(cg + 1); g02 = __ldg(cg + 2);
         g11 = __ldg(cg + 3); g12 = __ldg(cg + 4); g22 = __ldg(cg + 5);
       }
-      const int nq2 = nq * nq;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int q2 = G * b + g;
         float* dl = d + g * 4 * E;   // [val | dz | dy | dx] along q3, becomes [hv | hz | hy | hx]
         // points (q1, q2, q3) of this line: q3 < nq exist when the line does
-        const bool line = q1 < nq && q2 < nq;
+        const bool line = QF || (q1 < nq && q2 < nq);
         const float* pc = geo.ptC + (size_t)e * nq3 + q1 + nq * q2;
         const float* pg0 = GEN ? geo.ptG + (size_t)e * 6 * nq3 + q1 + nq * q2 : nullptr;
 #pragma unroll
         for (int q3 = 0; q3 < E; ++q3) {
           float hx = 0.f, hy = 0.f, hz = 0.f, cv = 0.f;
-          if (line && q3 < nq) {
+          if (QF || (line && q3 < nq)) {
             cv = __ldg(pc + q3 * nq2);
             if (GEN) {
               const float* pg = pg0 + q3 * nq2;
@@ -410,40 +534,86 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       if (L < SH::LINES) tc_write_transposed<SH, 2, false, SH::Kr(5)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(5, Mb)
+    if constexpr (TMA) {
+      // ---- result box (the A buffer is free once B-x is complete), then one
+      // bulk reduce-add into Y ----
 #pragma unroll 1
-    for (int j = 0; j < T; ++j) {   // B-x and assembly: row (i3, b), lines i2 = G b + g, D = [g][i1]
-      float d[SH::Nr(5)];
-      tmem_load<SH::Nr(5)>(tlane + j * SH::Nr(5), d);
-      const int r = j * 128 + lt, L = r >> 3;
-      if (L >= SH::LINES || !vok) continue;
-      const int i3 = L / H;
-      if (i3 >= np) continue;
-      const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
-      const bool zcon = !((zv_all >> i3) & 1u);
-      const bool zfirst = (zf_all >> i3) & 1u;
-      TIO* yz = Y + (size_t)gz * plane + v0 + v;
-      // every read of Y (the partial sums of earlier colours) is issued
-      // before the first store, so the loads overlap
-      float old[G * E];
+      for (int j = 0; j < T; ++j) {   // B-x: row (i3, b), lines i2 = G b + g, D = [g][i1]
+        float d[SH::Nr(5)];
+        tmem_load<SH::Nr(5)>(tlane + j * SH::Nr(5), d);
+        const int r = j * 128 + lt, L = r >> 3;
+        if (L >= SH::LINES) continue;
+        const int i3 = L / H, b = L % H;
+        if (i3 >= np) continue;
+        const bool zok = (zv_all >> i3) & 1u;
+        TIO* o = box + (i3 * np + G * b) * np * V + v;
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const unsigned rd = (zcon || !((yv >> g) & 1u)) ? 0u
-                            : xv & ~((zfirst && ((yf >> g) & 1u)) ? xf : 0u);
+        for (int g = 0; g < G; ++g) {
+          const int i2 = G * b + g;
+          if (i2 >= np) continue;
+          const unsigned ok = (zok && ((yv_all >> i2) & 1u)) ? xv : 0u;
 #pragma unroll
-        for (int i1 = 0; i1 < E; ++i1) old[g * E + i1] = ((rd >> i1) & 1u) ? tc_load(yz + yo[g] + xo[i1]) : 0.f;
+          for (int i1 = 0; i1 < E; ++i1)
+            if (i1 < np) tc_store(o + (g * np + i1) * V, ((ok >> i1) & 1u) ? d[g * E + i1] : 0.f);
+        }
+        if (!clean && vok && (wx || wy || wz)) {   // seam nodes lie outside the box: added here
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const int i2 = G * b + g;
+            if (i2 >= np) continue;
+#pragma unroll
+            for (int i1 = 0; i1 < E; ++i1) {
+              if (i1 >= np || !((wx && i1 == P) || (wy && i2 == P) || (wz && i3 == P))) continue;
+              const size_t node = (size_t)node_coord(cx, i1, P, m.Nx, m.periodic) +
+                                  (size_t)m.Nx * (node_coord(cy, i2, P, m.Ny, m.periodic) +
+                                                  (size_t)m.Ny * node_coord(cz, i3, P, m.Nz, m.periodic));
+              tc_atomic_add(Y + node * n_vec + v0 + v, d[g * E + i1]);
+            }
+          }
+        }
       }
+      fence_async_smem();
+      slot_sync(bar);
+      if (lt == 0) {
+        tma_reduce_add_4d(&ymap, box, v0, cx * P, cy * P, cz * P);
+        bulk_commit();
+      }
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < T; ++j) {   // B-x and assembly: row (i3, b), lines i2 = G b + g, D = [g][i1]
+        float d[SH::Nr(5)];
+        tmem_load<SH::Nr(5)>(tlane + j * SH::Nr(5), d);
+        const int r = j * 128 + lt, L = r >> 3;
+        if (L >= SH::LINES || !vok) continue;
+        const int i3 = L / H;
+        if (i3 >= np) continue;
+        const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
+        const bool zcon = !((zv_all >> i3) & 1u);
+        const bool zfirst = (zf_all >> i3) & 1u;
+        TIO* yz = Y + (size_t)gz * plane + v0 + v;
+        // every read of Y (the partial sums of earlier colours) is issued
+        // before the first store, so the loads overlap
+        float old[G * E];
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        if (G * bq + g >= np) continue;
-        const bool ycon = zcon || !((yv >> g) & 1u);
-        const unsigned first = (zfirst && ((yf >> g) & 1u)) ? xf : 0u;
-        const unsigned valid = ycon ? 0u : xv;
+        for (int g = 0; g < G; ++g) {
+          const unsigned rd = (zcon || !((yv >> g) & 1u)) ? 0u
+                              : xv & ~((zfirst && ((yf >> g) & 1u)) ? xf : 0u);
 #pragma unroll
-        for (int i1 = 0; i1 < E; ++i1) {
-          if (i1 >= np) continue;
-          TIO* dst = yz + yo[g] + xo[i1];
-          if ((first >> i1) & 1u) tc_store(dst, ((valid >> i1) & 1u) ? d[g * E + i1] : 0.f);
-          else if ((valid >> i1) & 1u) tc_store(dst, old[g * E + i1] + d[g * E + i1]);
+          for (int i1 = 0; i1 < E; ++i1) old[g * E + i1] = ((rd >> i1) & 1u) ? tc_load(yz + yo[g] + xo[i1]) : 0.f;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          if (G * bq + g >= np) continue;
+          const bool ycon = zcon || !((yv >> g) & 1u);
+          const unsigned first = (zfirst && ((yf >> g) & 1u)) ? xf : 0u;
+          const unsigned valid = ycon ? 0u : xv;
+#pragma unroll
+          for (int i1 = 0; i1 < E; ++i1) {
+            if (i1 >= np) continue;
+            TIO* dst = yz + yo[g] + xo[i1];
+            if ((first >> i1) & 1u) tc_store(dst, ((valid >> i1) & 1u) ? d[g * E + i1] : 0.f);
+            else if ((valid >> i1) & 1u) tc_store(dst, old[g * E + i1] + d[g * E + i1]);
+          }
         }
       }
     }
@@ -452,9 +622,14 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
 
   if (fail && lt == 0) {
     atomicMax(args.status, (int)FE_ETIMEOUT);
-    // let any MMA of this slot still in flight finish before the tensor memory is released
+    // let any MMA or box load of this slot still in flight finish before the
+    // shared and tensor memory are released
     mbar_wait_timed(mbar, 0, 100000000ull);
     mbar_wait_timed(mbar, 1, 100000000ull);
+    if (load_pending) mbar_wait_timed(lbar, lphase, 100000000ull);
+  }
+  if constexpr (TMA) {
+    if (lt == 0) bulk_wait_all();   // the reduces of this slot are complete
   }
   tc_fence_before();
   __syncthreads();

@@ -5,7 +5,10 @@ Every degree and quadrature size the kernel covers (n_p, n_q <= 8), Dirichlet
 and periodic boxes (odd cell counts: three colours along a direction),
 distorted trilinear cells (per-point metric), ragged vector tails, one cell,
 one vector.  The same cases run through the warp-level MMA kernel
-(fe_set_tile variant 1) as a cross-check.  Inputs are rounded to the storage
+(fe_set_tile variant 1) as a cross-check, and through the tcgen05 kernel with
+per-thread loads and stores (variant 2); variant 0 moves cell tiles with TMA
+boxes and bulk reduce-adds wherever n_vec fills whole 16-byte units (the
+n_vec = 8, 16, 24, 40 cases), else falls back to the thread path.  Inputs are rounded to the storage
 type first and the oracle is applied to the rounded inputs, so the comparison
 measures the arithmetic only.
 
@@ -74,6 +77,10 @@ CASES = [
     (3, 2, 2, 2, 5, False, False, 0, 9),      # n_q = n_p + 2 at p=2
     (1, 1, 1, 2, 4, False, False, 0, 3),      # one cell
     (4, 3, 5, 3, 5, True, True, 0, 8),        # periodic and distorted together, odd counts
+    (3, 3, 3, 6, 8, False, False, 0, 24),     # Dirichlet p=6, n_q = 8 (the n_q = E kernel), 3 vector blocks
+    (3, 2, 3, 6, 8, True, True, 0, 40),       # periodic seams along x/y/z, distorted, 5 vector blocks
+    (2, 3, 3, 4, 5, True, False, 0, 12),      # FP32 storage: box with a half-empty last vector block
+    (3, 2, 2, 1, 2, True, False, 0, 16),      # p=1 periodic: most of the box is guard and padding
 ]
 
 
@@ -81,7 +88,7 @@ def _case_id(c):
     return f"{c[0]}x{c[1]}x{c[2]}_p{c[3]}_q{c[4]}_{'per' if c[5] else 'dir'}{'_dist' if c[6] else ''}_nv{c[8]}"
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["tcgen05", "warp_mma"])
+@pytest.mark.parametrize("variant", [0, 1, 2], ids=["tcgen05", "warp_mma", "tcgen05_threads"])
 @pytest.mark.parametrize("mode", ["tf32", "bf16", "bf16s"])
 @pytest.mark.parametrize("case", CASES, ids=_case_id)
 def test_tc_matches_oracle(fe, case, mode, variant):
@@ -90,8 +97,7 @@ def test_tc_matches_oracle(fe, case, mode, variant):
         pytest.skip("BF16 storage runs on the tcgen05 kernel only")
     ctx, mesh, Vo = _pair(fe, nx, ny, nz, p, nq, periodic, distorted, quad, seed=p)
     try:
-        if mode != "bf16s":
-            fe.fe_set_tile(ctx, mode, 8, 8, variant)
+        fe.fe_set_tile(ctx, mode, 8, 8, variant)
         X = inputs.random_block(fe.fe_num_dofs(ctx), n_vec, "uniform", seed=11 + p)
         Y, Xr = _apply(fe, ctx, X, mode)
         Yref = orc.apply(mesh, p, nq, Xr, kind=quad, Vq=Vo)
@@ -144,7 +150,8 @@ def test_tc_many_tasks_per_cta(fe):
 
 def test_tc_unsupported_shapes(fe):
     """BF16 storage needs the tcgen05 kernel (n_p, n_q <= 8); FE_TF32 and
-    FE_BF16 fall back to the warp-MMA kernel there; variant 2 is invalid."""
+    FE_BF16 fall back to the warp-MMA kernel there; variant 3 is invalid, and
+    so is the warp-MMA kernel for BF16 storage."""
     ctx = fe.fe_setup(2, 2, 2, 8, 10)
     try:
         fe.fe_set_mode(ctx, "bf16s")
@@ -153,6 +160,51 @@ def test_tc_unsupported_shapes(fe):
             fe.fe_apply(ctx, X, torch.empty_like(X))
         assert ei.value.status == fe.FE_EUNSUPPORTED
         with pytest.raises(fe.FeError):
-            fe.fe_set_tile(ctx, "tf32", 8, 8, 2)
+            fe.fe_set_tile(ctx, "tf32", 8, 8, 3)
+        with pytest.raises(fe.FeError):
+            fe.fe_set_tile(ctx, "bf16s", 8, 8, 1)
     finally:
         fe.fe_destroy(ctx)
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16", "bf16s"])
+def test_tc_tma_path_equals_thread_path(fe, mode):
+    """The TMA boxes with bulk reduce-adds and the per-thread loads and stores
+    form every node's sum in the same order (Y starts at zero, colours run in
+    order, and the first colour's store equals 0 + its value), so FP32
+    storage gives bitwise the same Y.  BF16 storage rounds each colour's
+    contribution to bfloat16 before the reduce adds it, the thread path adds
+    it in FP32 and rounds the sum once: the two differ by a few bfloat16
+    roundings of the partial sums (at most 8 per node).  Dirichlet and periodic boxes, several vector blocks,
+    unaligned blocks (which take the thread path under variant 0 too)."""
+    for periodic in (False, True):
+        ctx, mesh, Vo = _pair(fe, 3, 4, 3, 6, 8, periodic=periodic, seed=9)
+        try:
+            fe.fe_set_mode(ctx, mode)
+            n = fe.fe_num_dofs(ctx)
+            X = torch.from_numpy(inputs.random_block(n, 32, "normal", 5)).to(device="cuda", dtype=fe.block_dtype(ctx))
+            Ys = []
+            for variant in (0, 2, 0):
+                fe.fe_set_tile(ctx, mode, 8, 8, variant)
+                Y = torch.full_like(X, float("nan"))
+                fe.fe_apply(ctx, X, Y)
+                Ys.append(Y)
+            torch.cuda.synchronize()
+            assert torch.equal(Ys[0], Ys[2])      # deterministic
+            if mode == "bf16s":
+                d = (Ys[0].double() - Ys[1].double()).abs().max().item()
+                assert d <= 2.0 ** -5 * Ys[1].double().abs().max().item(), d
+            else:
+                assert torch.equal(Ys[0], Ys[1])
+            # an unaligned block (offset by one element) takes the thread path
+            base = torch.empty(n * 32 + 8, dtype=X.dtype, device="cuda")
+            Xu = base[1:1 + n * 32].view(n, 32)
+            Xu.copy_(X)
+            Yu_base = torch.full_like(base, float("nan"))
+            Yu = Yu_base[1:1 + n * 32].view(n, 32)
+            fe.fe_set_tile(ctx, mode, 8, 8, 0)
+            fe.fe_apply(ctx, Xu, Yu)
+            torch.cuda.synchronize()
+            assert torch.equal(Yu, Ys[1])
+        finally:
+            fe.fe_destroy(ctx)
