@@ -22,8 +22,12 @@ using Shape8BF16 = TcShape<8, 2, kTcBF16>;
 // columns k' inputs, both in blocks of E (quantity, 1D index).  Forward
 // passes map nodes i to points q, backward passes points to nodes; N(q, i)
 // and D(q, i) are the value and derivative tables with sqrt(w_q) folded in.
+// With a metric g (box meshes: one G for every cell, entries 00 01 02 11 12
+// 22), B-z takes [c val | dz | dy | dx] and applies G itself:
+//   r_aa = N^T (c val) + D^T (g02 dx + g12 dy + g22 dz),
+//   r_ab = N^T (g01 dx + g11 dy + g12 dz),  r_ba = N^T (g00 dx + g01 dy + g02 dz).
 double tc_bline(int s, int E, int np, int nq, const std::vector<double>& Nf, const std::vector<double>& Df1, int nn,
-                int kk) {
+                int kk, const double* g) {
   const int nb = nn / E, kb = kk / E;
   const bool fwd = s <= 2;
   const int q = fwd ? nn % E : kk % E, i = fwd ? kk % E : nn % E;
@@ -36,6 +40,11 @@ double tc_bline(int s, int E, int np, int nq, const std::vector<double>& Nf, con
       return (nb == 0 && kb == 0) ? Nv : (nb == 1 && kb == 0) ? Dv : (nb == 2 && kb == 1) ? Nv
              : (nb == 3 && kb == 2) ? Nv : 0.0;
     case 3:                                                                              // <- [hv hz hy hx]
+      if (g != nullptr) {                                                                // <- [c val dz dy dx]
+        static const int row[3][3] = {{5, 4, 2}, {4, 3, 1}, {2, 1, 0}};   // G entry of (output, dz/dy/dx)
+        if (kb == 0) return nb == 0 ? Nv : 0.0;
+        return g[row[nb][kb - 1]] * (nb == 0 ? Dv : Nv);
+      }
       return (nb == 0 && kb == 0) ? Nv : (nb == 0 && kb == 1) ? Dv : (nb == 1 && kb == 2) ? Nv
              : (nb == 2 && kb == 3) ? Nv : 0.0;
     case 4: return (nb == 0 && kb == 0) ? Nv : (nb == 0 && kb == 1) ? Dv : (nb == 1 && kb == 2) ? Nv : 0.0;
@@ -58,7 +67,7 @@ uint16_t bf16_bits(double x) {
 }
 
 template <class SH>
-std::vector<unsigned char> tc_image(const fe_ctx* c) {
+std::vector<unsigned char> tc_image(const fe_ctx* c, const double* g) {
   constexpr int E = SH::E, G = SH::G;
   const int np = c->np, nq = c->nq;
   // derivative of the shape functions at the points, sqrt(w_q) folded in:
@@ -75,7 +84,7 @@ std::vector<unsigned char> tc_image(const fe_ctx* c) {
     const int KL = tc_kline(s) * E, NL = tc_nline(s) * E;
     for (int nn = 0; nn < NL; ++nn)
       for (int kk = 0; kk < KL; ++kk) {
-        const double v = tc_bline(s, E, np, nq, c->Nf, Df1, nn, kk);
+        const double v = tc_bline(s, E, np, nq, c->Nf, Df1, nn, kk, g);
         for (int g = 0; g < G; ++g) {
           unsigned char* p = img.data() + SH::b_off(s) + tc_off<SH::ES>(g * NL + nn, g * KL + kk, SH::Kr(s));
           if (SH::KIND == kTcTF32) {
@@ -212,7 +221,17 @@ static std::vector<unsigned long long> tc_cell_masks(const fe_ctx* c) {
 
 cudaError_t build_tc_images(fe_ctx* c) {
   if (c->refined || c->np > 8 || c->nq > 8) return cudaSuccess;   // no tcgen05 kernel for this shape
-  const std::vector<unsigned char> t = tc_image<Shape8TF32>(c), b = tc_image<Shape8BF16>(c);
+  // Box meshes: every cell has the same metric (the same diagonal Jacobian;
+  // the FP64 values of different cells agree to rounding), folded into B-z.
+  const double* g = nullptr;
+  if (!c->general) {
+    g = c->cellG.data();
+    for (size_t e = 1; e < c->n_cells; ++e)
+      for (int k = 0; k < 6; ++k)
+        if (std::fabs(c->cellG[e * 6 + k] - g[k]) > 1e-12 * (std::fabs(g[k]) + std::fabs(g[0])))
+          return cudaSuccess;   // not one metric: no tcgen05 kernel
+  }
+  const std::vector<unsigned char> t = tc_image<Shape8TF32>(c, g), b = tc_image<Shape8BF16>(c, g);
   const std::vector<unsigned long long> masks = tc_cell_masks(c);
   cudaError_t e = cudaMalloc(&c->d_tcmask, masks.size() * sizeof(unsigned long long));
   if (e == cudaSuccess)

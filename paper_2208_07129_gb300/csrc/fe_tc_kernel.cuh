@@ -17,6 +17,8 @@
 //        [hx hy hz] = G [dx dy dz] (G = mu det J J^-1 J^-T), hv = c val
 //        (c = det J V); weights are folded into N and D as sqrt(w)
 //   B-z: r_aa = N_z^T hv + D_z^T hz, r_ab = N_z^T hy, r_ba = N_z^T hx
+//        (box meshes: every cell has the same G, which is folded into the
+//        B operand of B-z, so only hv = c val is formed per point)
 //   B-y: r_a = N_y^T r_aa + D_y^T r_ab, r_b = N_y^T r_ba
 //   B-x: out = N_x^T r_a + D_x^T r_b, then the colour-ordered scatter.
 // N and D here are the 1D value and derivative matrices at the quadrature
@@ -224,6 +226,14 @@ __host__ __device__ constexpr int tc_guard_rows(int np) {
   return (E - 1) * (np + 1) - np * np + 1 > 0 ? (E - 1) * (np + 1) - np * np + 1 : 0;
 }
 
+// Largest loaded box with its guard rows, in node rows, over n_p = 2 .. E.
+template <int E>
+__host__ __device__ constexpr int tc_box_rows_max() {
+  int m = 0;
+  for (int n = 2; n <= E; ++n) m = n * n * n + tc_guard_rows<E>(n) > m ? n * n * n + tc_guard_rows<E>(n) : m;
+  return m;
+}
+
 template <typename TIO>
 __device__ __forceinline__ TIO tc_zero() {
   if constexpr (sizeof(TIO) == 4) return 0.f;
@@ -251,7 +261,11 @@ __device__ __forceinline__ void tc_atomic_add(__nv_bfloat16* p, float v) { atomi
 // by the threads.  Without TMA (n_vec not a multiple of 16 bytes, unaligned
 // blocks, or fe_set_tile variant 2) every thread loads and stores its own
 // values, first writers storing and later colours adding.
-// QF: n_q = E, so every quadrature point of the padded lines exists.
+// QF: n_q = E, so every quadrature point of the padded lines exists; with
+// TMA, the cell's c values are then staged by one bulk copy into the F-x
+// operand buffer once F-x has read it.
+// GEN: per-point metric (trilinear cells); otherwise the one metric of the
+// box mesh is part of the B operand of B-z and the point operation is c val.
 template <int E, int G, int KIND, typename TIO, bool GEN, bool TMA, bool QF>
 __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
     tc_apply_kernel(const TcArgs args, const MeshDev m, const Geom<float> geo, const int* __restrict__ cells,
@@ -259,7 +273,15 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
                     const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap) {
   using SH = TcShape<E, G, KIND>;
   constexpr int H = SH::H, T = SH::T, SLOTS = SH::SLOTS, V = kTcVectors;
-  static_assert(!TMA || (E * E * E + 32) * V * (int)sizeof(TIO) <= SH::M_BYTES, "a cell box fits the A buffer");
+  // A buffer (Mb) during a task with TMA: the result box at offset 0 (after
+  // B-x), the next task's loaded box from BOX_IN on (issued once B-y is
+  // complete; until then the operands of F-y ... B-y use the whole buffer,
+  // and from then on the operand of B-x lies below BOX_IN)
+  constexpr int BOX_OUT_MAX = E * E * E * V * (int)sizeof(TIO);
+  constexpr int BX_A = 128 * SH::T * SH::Kr(5) * SH::ES;
+  constexpr int BOX_IN = (BX_A > BOX_OUT_MAX ? BX_A : BOX_OUT_MAX + 127) / 128 * 128;
+  static_assert(!TMA || BOX_IN + tc_box_rows_max<E>() * V * (int)sizeof(TIO) <= SH::M_BYTES,
+                "result box, B-x operand and the next loaded box fit the A buffer");
   static_assert(SH::B_BYTES % 128 == 0 && SH::SLOT_BYTES % 128 == 0 && SH::S_BYTES % 128 == 0,
                 "A buffers start 128 bytes apart");
   extern __shared__ __align__(128) unsigned char smem[];
@@ -271,11 +293,14 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
   uint64_t* mbar = mbars + slot;            // MMA completions (six per task)
   uint64_t* lbar = mbars + SLOTS + slot;    // box loads (one per task)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbars + 2 * SLOTS);
-  TIO* box = reinterpret_cast<TIO*>(Mb);
+  TIO* box = reinterpret_cast<TIO*>(Mb);              // result box
+  TIO* box_in = reinterpret_cast<TIO*>(Mb + BOX_IN);   // loaded box
   const int bar = 1 + slot;
   const int np = args.np, nq = QF ? E : args.nq, P = np - 1;
   const int nq2 = nq * nq, nq3 = nq2 * nq;
   const int np2 = np * np, np3 = np2 * np;
+  // the cell's c values (n_q^3 floats, contiguous) are staged in shared memory
+  constexpr bool CVS = TMA && QF;
   if constexpr (TMA) {
     // box destinations must be 128-byte aligned; the layout keeps every A
     // buffer at a multiple of 128 bytes from the base of shared memory
@@ -357,17 +382,19 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       wy = m.periodic && cy == m.ny - 1;
       wz = m.periodic && cz == m.nz - 1;
       clean = xv == full && yv_all == full && zv_all == full && !(wx || wy || wz);
-      if (lt == 0) {
-        bulk_wait_read_all();   // the previous task's reduce has read its result box
-        mbar_arrive_expect_tx(lbar, (uint32_t)(np3 * V * (int)sizeof(TIO)));
-        tma_load_4d(box, &xmap, v0, cx * P, cy * P, cz * P, lbar);
-      }
-      {
+      // the previous task's reduce has read its result box before F-y's
+      // operand overwrites it (the barrier below orders every later write)
+      if (lt == 0) bulk_wait_read_all();
+      if (task == (int)blockIdx.x * SLOTS + slot) {   // first task: nothing prefetched
+        if (lt == 0) {
+          mbar_arrive_expect_tx(lbar, (uint32_t)(np3 * V * (int)sizeof(TIO)));
+          tma_load_4d(box_in, &xmap, v0, cx * P, cy * P, cz * P, lbar);
+        }
         const int words = tc_guard_rows<E>(np) * V * (int)sizeof(TIO) / 16;
-        uint4* gz = reinterpret_cast<uint4*>(Mb + np3 * V * (int)sizeof(TIO));
+        uint4* gz = reinterpret_cast<uint4*>(box_in + np3 * V);
         for (int k = lt; k < words; k += 128) gz[k] = make_uint4(0, 0, 0, 0);
+        load_pending = true;
       }
-      load_pending = true;
       if (slot_sync_or(bar, !mbar_wait_timed(lbar, lphase))) {
         fail = true;
         break;
@@ -377,7 +404,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       if (!clean) {   // the same for every thread of the slot
         for (int n = lt; n < np3; n += 128) {
           const int i1 = n % np, i2 = (n / np) % np, i3 = n / np2;
-          TIO* row = box + n * V;
+          TIO* row = box_in + n * V;
           if (!((xv >> i1) & (yv_all >> i2) & (zv_all >> i3) & 1u)) {
 #pragma unroll
             for (int k = 0; k < V; ++k) row[k] = tc_zero<TIO>();
@@ -401,7 +428,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
 #pragma unroll
         for (int k = 0; k < SH::Kr(0); ++k) vals[k] = 0.f;
         if (i3 < np) {
-          const TIO* s0 = box + (i3 * np + G * (L % H)) * np * V + v;
+          const TIO* s0 = box_in + (i3 * np + G * (L % H)) * np * V + v;
 #pragma unroll
           for (int g = 0; g < G; ++g) {
             const TIO* sg = s0 + g * np * V;
@@ -445,18 +472,26 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
     // next A may overwrite this one as soon as the pass is complete.
     // Only the slot's first warp polls the mbarrier; the other three sleep
     // in the named barrier that follows.
-#define FE_TC_ISSUE(S, ABUF)                                                   \
+#define FE_TC_ISSUE_X(S, ABUF, EXTRA_FAIL)                                     \
   fence_async_smem();                                                          \
   tc_fence_before();                                                           \
   slot_sync(bar);                                                              \
   if (lt == 0) tc_issue<SH, S>(tmem, ABUF, Bs, mbar);                          \
-  if (slot_sync_or(bar, lt < 32 && !mbar_wait_timed(mbar, (S) & 1))) {         \
+  if (slot_sync_or(bar, (lt < 32 && !mbar_wait_timed(mbar, (S) & 1)) || (EXTRA_FAIL))) { \
     fail = true;                                                               \
     break;                                                                     \
   }                                                                            \
   tc_fence_after();
+#define FE_TC_ISSUE(S, ABUF) FE_TC_ISSUE_X(S, ABUF, false)
 
     FE_TC_ISSUE(0, Sb)
+    if constexpr (CVS) {   // F-x has read its operand: the cell's c values take its place
+      if (lt == 0) {
+        mbar_arrive_expect_tx(lbar, (uint32_t)(E * E * E * sizeof(float)));
+        bulk_load(Sb, geo.ptC + (size_t)e * (E * E * E), (uint32_t)(E * E * E * sizeof(float)), lbar);
+      }
+      load_pending = true;
+    }
 #pragma unroll 1
     for (int j = 0; j < T; ++j) {   // F-x: row (i3, b), lines i2 -> A of F-y: (q1, i3 / G)
       float d[SH::Nr(0)];
@@ -472,7 +507,11 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       const int r = j * 128 + lt, L = r >> 3;
       if (L < SH::LINES) tc_write_transposed<SH, 3, false, SH::Kr(2)>(d, L / H, L % H, r & 7, Mb);
     }
-    FE_TC_ISSUE(2, Mb)
+    FE_TC_ISSUE_X(2, Mb, CVS && !mbar_wait_timed(lbar, lphase))
+    if constexpr (CVS) {
+      load_pending = false;
+      lphase ^= 1u;
+    }
 #pragma unroll 1
     for (int j = 0; j < T; ++j) {   // F-z and the quadrature-point operation: row (q1, b), lines q2 = G b + g
       float d[SH::Nr(2)];
@@ -480,39 +519,32 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       const int r = j * 128 + lt, L = r >> 3;
       if (L >= SH::LINES) continue;
       const int q1 = L / H, b = L % H;
-      float g00 = 0.f, g01 = 0.f, g02 = 0.f, g11 = 0.f, g12 = 0.f, g22 = 0.f;
-      if (!GEN) {
-        const float* cg = geo.cellG + (size_t)e * 6;
-        g00 = __ldg(cg); g01 = __ldg(cg + 1); g02 = __ldg(cg + 2);
-        g11 = __ldg(cg + 3); g12 = __ldg(cg + 4); g22 = __ldg(cg + 5);
-      }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int q2 = G * b + g;
         float* dl = d + g * 4 * E;   // [val | dz | dy | dx] along q3, becomes [hv | hz | hy | hx]
         // points (q1, q2, q3) of this line: q3 < nq exist when the line does
+        // (values at padded points meet zero B entries in B-z)
         const bool line = QF || (q1 < nq && q2 < nq);
-        const float* pc = geo.ptC + (size_t)e * nq3 + q1 + nq * q2;
+        const float* pc = CVS ? reinterpret_cast<const float*>(Sb) + q1 + E * q2
+                              : geo.ptC + (size_t)e * nq3 + q1 + nq * q2;
         const float* pg0 = GEN ? geo.ptG + (size_t)e * 6 * nq3 + q1 + nq * q2 : nullptr;
 #pragma unroll
         for (int q3 = 0; q3 < E; ++q3) {
-          float hx = 0.f, hy = 0.f, hz = 0.f, cv = 0.f;
+          float cv = 0.f;
           if (QF || (line && q3 < nq)) {
-            cv = __ldg(pc + q3 * nq2);
+            cv = CVS ? pc[q3 * E * E] : __ldg(pc + q3 * nq2);
             if (GEN) {
               const float* pg = pg0 + q3 * nq2;
-              g00 = __ldg(pg); g01 = __ldg(pg + nq3); g02 = __ldg(pg + 2 * nq3);
-              g11 = __ldg(pg + 3 * nq3); g12 = __ldg(pg + 4 * nq3); g22 = __ldg(pg + 5 * nq3);
+              const float g00 = __ldg(pg), g01 = __ldg(pg + nq3), g02 = __ldg(pg + 2 * nq3);
+              const float g11 = __ldg(pg + 3 * nq3), g12 = __ldg(pg + 4 * nq3), g22 = __ldg(pg + 5 * nq3);
+              const float dz = dl[E + q3], dy = dl[2 * E + q3], dx = dl[3 * E + q3];
+              dl[E + q3] = g02 * dx + g12 * dy + g22 * dz;
+              dl[2 * E + q3] = g01 * dx + g11 * dy + g12 * dz;
+              dl[3 * E + q3] = g00 * dx + g01 * dy + g02 * dz;
             }
-            const float dz = dl[E + q3], dy = dl[2 * E + q3], dx = dl[3 * E + q3];
-            hx = g00 * dx + g01 * dy + g02 * dz;
-            hy = g01 * dx + g11 * dy + g12 * dz;
-            hz = g02 * dx + g12 * dy + g22 * dz;
           }
           dl[q3] = cv * dl[q3];
-          dl[E + q3] = hz;
-          dl[2 * E + q3] = hy;
-          dl[3 * E + q3] = hx;
         }
       }
       tc_write_row<SH, SH::Kr(3)>(d, r, Mb);
@@ -526,6 +558,21 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       if (L < SH::LINES) tc_write_transposed<SH, 3, true, SH::Kr(4)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(4, Mb)
+    if constexpr (TMA) {   // prefetch the next task's box
+      const int nt = task + (int)gridDim.x * SLOTS;
+      if (nt < n_tasks) {
+        if (lt == 0) {
+          const int e2 = cells[nt / n_vb];
+          const int cx2 = e2 % m.nx, cy2 = (e2 / m.nx) % m.ny, cz2 = e2 / (m.nx * m.ny);
+          mbar_arrive_expect_tx(lbar, (uint32_t)(np3 * V * (int)sizeof(TIO)));
+          tma_load_4d(box_in, &xmap, (nt % n_vb) * kTcVectors, cx2 * P, cy2 * P, cz2 * P, lbar);
+        }
+        const int words = tc_guard_rows<E>(np) * V * (int)sizeof(TIO) / 16;
+        uint4* gz = reinterpret_cast<uint4*>(box_in + np3 * V);
+        for (int k = lt; k < words; k += 128) gz[k] = make_uint4(0, 0, 0, 0);
+        load_pending = true;
+      }
+    }
 #pragma unroll 1
     for (int j = 0; j < T; ++j) {   // B-y: row (i3, b), lines q1 -> A of B-x: (i3, i2 / G)
       float d[SH::Nr(4)];
@@ -618,6 +665,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       }
     }
 #undef FE_TC_ISSUE
+#undef FE_TC_ISSUE_X
   }
 
   if (fail && lt == 0) {

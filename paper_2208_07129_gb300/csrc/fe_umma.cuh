@@ -62,17 +62,23 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // a count of polls: each poll may suspend the thread for up to hint_ns (it
 // resumes as soon as the phase completes), so a waiting warp takes few issue
 // slots.  Returns false once limit_ns have passed without completion.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t phase, uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(phase), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
+
+// The clock is read only once the first poll has come back empty.
 __device__ __forceinline__ bool mbar_wait_timed(uint64_t* mbar, uint32_t phase, uint64_t limit_ns = 2000000000ull,
                                                 uint32_t hint_ns = 100000u) {
+  if (mbar_try_wait(mbar, phase, hint_ns)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(phase), "r"(hint_ns)
-        : "memory");
-    if (done) return true;
+    if (mbar_try_wait(mbar, phase, hint_ns)) return true;
     if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
