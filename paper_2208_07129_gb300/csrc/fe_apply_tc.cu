@@ -15,6 +15,8 @@ namespace fe {
 
 namespace {
 
+constexpr int kTcQueues = 32;   // at least the largest colour count (27)
+
 using Shape8TF32 = TcShape<8, 2, kTcTF32>;
 using Shape8BF16 = TcShape<8, 2, kTcBF16>;
 
@@ -150,11 +152,14 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  // the bulk reduces add every colour's result to Y
+  // the bulk reduces add every colour's result to Y; every colour's task
+  // counter starts at zero
   if (TMA && (e = cudaMemsetAsync(Y, 0, c->n_dofs * (size_t)n_vec * sizeof(TIO), s)) != cudaSuccess) return e;
+  if (TMA && (e = cudaMemsetAsync(c->d_tcq, 0, kTcQueues * sizeof(int), s)) != cudaSuccess) return e;
   const Geom<float> geo = make_geom<float>(c);
-  TcArgs a{img, nullptr, c->np, c->nq, c->d_status};
+  TcArgs a{img, nullptr, c->np, c->nq, c->d_status, nullptr};
   const int n_vb = (n_vec + kTcVectors - 1) / kTcVectors;
+  if (TMA && c->colors.n_colors > kTcQueues) return cudaErrorInvalidValue;
   for (int k = 0; k < c->colors.n_colors; ++k) {
     const int n = c->colors.offset[k + 1] - c->colors.offset[k];
     if (n == 0) continue;
@@ -162,6 +167,7 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
     if (tasks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>((tasks + SH::SLOTS - 1) / SH::SLOTS, (long long)sms);
     a.cmask = c->d_tcmask + c->colors.offset[k];
+    a.queue = c->d_tcq + k;
     kern<<<grid, 128 * SH::SLOTS, smem, s>>>(a, c->mdev, geo, c->d_cells + c->colors.offset[k], (int)tasks, n_vec,
                                               n_vb, X, Y, xm, ym);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -236,6 +242,7 @@ cudaError_t build_tc_images(fe_ctx* c) {
   cudaError_t e = cudaMalloc(&c->d_tcmask, masks.size() * sizeof(unsigned long long));
   if (e == cudaSuccess)
     e = cudaMemcpy(c->d_tcmask, masks.data(), masks.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_tcq, kTcQueues * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_tcimg[0], t.size());
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tcimg[0], t.data(), t.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_tcimg[1], b.size());
@@ -244,7 +251,7 @@ cudaError_t build_tc_images(fe_ctx* c) {
 }
 
 bool tc_supported(const fe_ctx* c) {
-  return c->d_tcimg[0] != nullptr && c->d_tcimg[1] != nullptr && c->d_tcmask != nullptr;
+  return c->d_tcimg[0] != nullptr && c->d_tcimg[1] != nullptr && c->d_tcmask != nullptr && c->d_tcq != nullptr;
 }
 
 cudaError_t apply_tc(const fe_ctx* c, const void* X, void* Y, int n_vec, cudaStream_t s, fe_mode mode) {

@@ -166,6 +166,7 @@ struct fe_ctx {
   // per cell (colour order): bit masks of its nodes along x, y, z that exist
   // and are free, and of those it writes first (tcgen05 kernel)
   unsigned long long* d_tcmask = nullptr;
+  int* d_tcq = nullptr;     // tcgen05 TMA launches: one task counter per colour, zeroed by each product
   // small meshes (E n_p^3 <= kSmallSlots): per-cell result scratch for up to
   // 64 FP64 vectors, so that fe_apply runs as two launches instead of one per
   // colour; allocated at setup

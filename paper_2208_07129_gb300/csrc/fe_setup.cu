@@ -395,7 +395,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->d_cellG32); cudaFree(c->d_ptG32); cudaFree(c->d_ptC32); cudaFree(c->d_detJ);
   cudaFree(c->d_cellGff); cudaFree(c->d_ptGff); cudaFree(c->d_ptCff);
   cudaFree(c->d_status); cudaFree(c->d_stage);
-  cudaFree(c->d_tcimg[0]); cudaFree(c->d_tcimg[1]); cudaFree(c->d_tcmask); cudaFree(c->d_small);
+  cudaFree(c->d_tcimg[0]); cudaFree(c->d_tcimg[1]); cudaFree(c->d_tcmask); cudaFree(c->d_tcq); cudaFree(c->d_small);
   if (c->copy_in) cudaStreamDestroy(c->copy_in);
   if (c->copy_out) cudaStreamDestroy(c->copy_out);
   for (cudaEvent_t ev : {c->ev_start, c->ev_in[0], c->ev_in[1], c->ev_comp[0], c->ev_comp[1], c->ev_out[0], c->ev_out[1]})

@@ -129,6 +129,7 @@ struct TcArgs {
   const unsigned long long* cmask;   // per cell of the launch: node masks (see tc_cell_masks)
   int np, nq;
   int* status;                 // FE_ETIMEOUT is raised here when a bounded wait gives up
+  int* queue;                  // TMA kernels: task counter of the launch (zero at launch)
 };
 
 // Transposed write of one row of D (pass S) into the A layout of pass S + 1.
@@ -234,6 +235,14 @@ __host__ __device__ constexpr int tc_box_rows_max() {
   return m;
 }
 
+// Task nt exists and its box lies inside the node grid (not on a periodic seam).
+__device__ __forceinline__ bool tc_box_task(int nt, int n_tasks, int n_vb, const int* cells, const MeshDev& m) {
+  if (nt >= n_tasks) return false;
+  const int e = cells[nt / n_vb];
+  const int cx = e % m.nx, cy = (e / m.nx) % m.ny, cz = e / (m.nx * m.ny);
+  return !(m.periodic && (cx == m.nx - 1 || cy == m.ny - 1 || cz == m.nz - 1));
+}
+
 template <typename TIO>
 __device__ __forceinline__ TIO tc_zero() {
   if constexpr (sizeof(TIO) == 4) return 0.f;
@@ -250,17 +259,18 @@ __device__ __forceinline__ void tc_atomic_add(__nv_bfloat16* p, float v) { atomi
 // lt of every 128-row tile of a pass.
 //
 // TMA: the cell's values for the task's 8 vectors arrive as one tensor-map
-// box (8 vectors x n_p^3 nodes, dense) in the slot's A buffer; nodes that are
-// Dirichlet nodes are zeroed and nodes across a periodic seam (outside the
-// box) fetched by the threads, then every thread builds its rows of the F-x
-// operand from the box.  The result is written back into the same buffer as
-// a box of the same shape (Dirichlet nodes 0) and added to Y by one bulk
-// reduce; Y starts at zero, cells of one colour share no node, and colours
-// run in order, so every sum is formed in the same order as by the
-// colour-ordered stores and adds of the thread path.  Seam nodes are added
-// by the threads.  Without TMA (n_vec not a multiple of 16 bytes, unaligned
-// blocks, or fe_set_tile variant 2) every thread loads and stores its own
-// values, first writers storing and later colours adding.
+// box (8 vectors x n_p^3 nodes, dense) in the slot's A buffer (loaded while
+// the slot's previous task runs its last passes); Dirichlet nodes are zeroed,
+// then every thread builds its rows of the F-x operand from the box.  The
+// result is written into the same buffer as a box of the same shape
+// (Dirichlet nodes 0) and added to Y by one bulk reduce; Y starts at zero,
+// cells of one colour share no node, and colours run in order, so every sum
+// is formed in the same order as by the colour-ordered stores and adds of
+// the thread path.  Cells on a periodic seam, whose boxes would reach past
+// the end of the node grid, take the thread path.  Without TMA (n_vec not a
+// multiple of 16 bytes, unaligned blocks, or fe_set_tile variant 2) every
+// thread loads and stores its own values, first writers storing and later
+// colours adding.
 // QF: n_q = E, so every quadrature point of the padded lines exists; with
 // TMA, the cell's c values are then staged by one bulk copy into the F-x
 // operand buffer once F-x has read it.
@@ -293,6 +303,8 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
   uint64_t* mbar = mbars + slot;            // MMA completions (six per task)
   uint64_t* lbar = mbars + SLOTS + slot;    // box loads (one per task)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbars + 2 * SLOTS);
+  // per slot: 2 x (the task taken from the queue) + (its box is being loaded)
+  int* tnext = reinterpret_cast<int*>(tslot + 1);
   TIO* box = reinterpret_cast<TIO*>(Mb);              // result box
   TIO* box_in = reinterpret_cast<TIO*>(Mb + BOX_IN);   // loaded box
   const int bar = 1 + slot;
@@ -340,7 +352,22 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
   bool fail = false, load_pending = false;
   uint32_t lphase = 0;
 
-  for (int task = blockIdx.x * SLOTS + slot; task < n_tasks && !fail; task += gridDim.x * SLOTS) {
+  // TMA kernels take their tasks from the launch's counter, one at a time
+  // (the next one while the current task's last passes run), so that slots
+  // whose tasks take the thread path do not hold up the launch; otherwise
+  // slot s of CTA b takes tasks 4 b + s, 4 b + s + 4 grid, ...
+  int next_task = (int)blockIdx.x * SLOTS + slot;
+  if constexpr (TMA) {
+    if (lt == 0) tnext[slot] = atomicAdd(args.queue, 1);
+    slot_sync(bar);
+    next_task = tnext[slot];
+  }
+  for (int task = next_task; task < n_tasks && !fail; task = next_task) {
+    if constexpr (!TMA) next_task = task + (int)gridDim.x * SLOTS;
+    // TMA: thread 0 takes the next task now; the counter's answer is used
+    // once B-y is complete, long after it has arrived
+    int taken = 0;
+    if (TMA && lt == 0) taken = atomicAdd(args.queue, 1);
     const int e = cells[task / n_vb];
     const int v0 = (task % n_vb) * kTcVectors;
     const int cx = e % m.nx, cy = (e / m.nx) % m.ny, cz = e / (m.nx * m.ny);
@@ -355,15 +382,20 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
     const unsigned yv_all = (unsigned)((cm >> 16) & 0xffu), yf_all = (unsigned)((cm >> 24) & 0xffu);
     const unsigned zv_all = (unsigned)((cm >> 32) & 0xffu), zf_all = (unsigned)((cm >> 40) & 0xffu);
     const size_t plane = (size_t)m.Nx * m.Ny * n_vec;
+    // The cell lies across a periodic seam (its box would reach past the end
+    // of the node grid along x / y / z).  With TMA, such a cell takes the
+    // thread path: a box that reaches outside the tensor is moved at a much
+    // lower rate than one inside it.
+    const bool seam = m.periodic && (cx == m.nx - 1 || cy == m.ny - 1 || cz == m.nz - 1);
+    const bool thr = !TMA || seam;
     // thread path: element offsets along x (all E entries) and along the
     // thread's G lines in y
-    int xo[TMA ? 1 : E];
-    int yo[TMA ? 1 : G];
+    int xo[E];
+    int yo[G];
     unsigned yv = 0, yf = 0;
-    // TMA path: the cell lies across a periodic seam along x / y / z; a
-    // "clean" cell has neither seam nor Dirichlet node
-    bool wx = false, wy = false, wz = false, clean = true;
-    if constexpr (!TMA) {
+    // TMA path: a "clean" cell has no Dirichlet node
+    bool clean = true;
+    if (thr) {
 #pragma unroll
       for (int i = 0; i < E; ++i) xo[i] = node_coord(cx, i, P, m.Nx, m.periodic) * n_vec;
 #pragma unroll
@@ -375,17 +407,15 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       }
     }
 
-    if constexpr (TMA) {
-      // ---- gather: one box load, seam and Dirichlet fix-ups, operand rows ----
+    if (TMA && !thr) {
+      // ---- gather: one box load (prefetched by the previous task unless
+      // this is the slot's first box), Dirichlet nodes zeroed, operand rows ----
       const unsigned full = (1u << np) - 1u;
-      wx = m.periodic && cx == m.nx - 1;
-      wy = m.periodic && cy == m.ny - 1;
-      wz = m.periodic && cz == m.nz - 1;
-      clean = xv == full && yv_all == full && zv_all == full && !(wx || wy || wz);
+      clean = xv == full && yv_all == full && zv_all == full;
       // the previous task's reduce has read its result box before F-y's
       // operand overwrites it (the barrier below orders every later write)
       if (lt == 0) bulk_wait_read_all();
-      if (task == (int)blockIdx.x * SLOTS + slot) {   // first task: nothing prefetched
+      if (!load_pending) {   // nothing prefetched for this task
         if (lt == 0) {
           mbar_arrive_expect_tx(lbar, (uint32_t)(np3 * V * (int)sizeof(TIO)));
           tma_load_4d(box_in, &xmap, v0, cx * P, cy * P, cz * P, lbar);
@@ -404,17 +434,10 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       if (!clean) {   // the same for every thread of the slot
         for (int n = lt; n < np3; n += 128) {
           const int i1 = n % np, i2 = (n / np) % np, i3 = n / np2;
-          TIO* row = box_in + n * V;
           if (!((xv >> i1) & (yv_all >> i2) & (zv_all >> i3) & 1u)) {
+            TIO* row = box_in + n * V;
 #pragma unroll
             for (int k = 0; k < V; ++k) row[k] = tc_zero<TIO>();
-          } else if ((wx && i1 == P) || (wy && i2 == P) || (wz && i3 == P)) {
-            const size_t node = (size_t)node_coord(cx, i1, P, m.Nx, m.periodic) +
-                                (size_t)m.Nx * (node_coord(cy, i2, P, m.Ny, m.periodic) +
-                                                (size_t)m.Ny * node_coord(cz, i3, P, m.Nz, m.periodic));
-            const TIO* src = X + node * n_vec + v0;
-#pragma unroll
-            for (int k = 0; k < V; ++k) row[k] = v0 + k < n_vec ? src[k] : tc_zero<TIO>();
           }
         }
         slot_sync(bar);
@@ -462,7 +485,6 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
         tc_write_row<SH, SH::Kr(0)>(vals, r, Sb);
       }
     }
-
     // ---- the six passes ----
     // pass index s = 0..5, mbarrier phase = s & 1 (six completions per task).
     // Every thread's writes of the A operand become visible to the tensor
@@ -558,19 +580,18 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       if (L < SH::LINES) tc_write_transposed<SH, 3, true, SH::Kr(4)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(4, Mb)
-    if constexpr (TMA) {   // prefetch the next task's box
-      const int nt = task + (int)gridDim.x * SLOTS;
-      if (nt < n_tasks) {
-        if (lt == 0) {
+    if constexpr (TMA) {   // take the next task; prefetch its box unless it takes the thread path
+      if (lt == 0) {
+        const int nt = taken;
+        const bool pf = tc_box_task(nt, n_tasks, n_vb, cells, m);
+        tnext[slot] = 2 * nt + (pf ? 1 : 0);
+        if (pf) {
           const int e2 = cells[nt / n_vb];
           const int cx2 = e2 % m.nx, cy2 = (e2 / m.nx) % m.ny, cz2 = e2 / (m.nx * m.ny);
           mbar_arrive_expect_tx(lbar, (uint32_t)(np3 * V * (int)sizeof(TIO)));
           tma_load_4d(box_in, &xmap, (nt % n_vb) * kTcVectors, cx2 * P, cy2 * P, cz2 * P, lbar);
+          load_pending = true;
         }
-        const int words = tc_guard_rows<E>(np) * V * (int)sizeof(TIO) / 16;
-        uint4* gz = reinterpret_cast<uint4*>(box_in + np3 * V);
-        for (int k = lt; k < words; k += 128) gz[k] = make_uint4(0, 0, 0, 0);
-        load_pending = true;
       }
     }
 #pragma unroll 1
@@ -581,7 +602,17 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       if (L < SH::LINES) tc_write_transposed<SH, 2, false, SH::Kr(5)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(5, Mb)
-    if constexpr (TMA) {
+    if constexpr (TMA) {   // the task thread 0 took, and whether its box is loading
+      const int tn = tnext[slot];   // written before the barrier above
+      next_task = tn >> 1;
+      if (tn & 1) {
+        const int words = tc_guard_rows<E>(np) * V * (int)sizeof(TIO) / 16;
+        uint4* gz = reinterpret_cast<uint4*>(box_in + np3 * V);
+        for (int k = lt; k < words; k += 128) gz[k] = make_uint4(0, 0, 0, 0);
+        load_pending = true;
+      }
+    }
+    if (TMA && !thr) {
       // ---- result box (the A buffer is free once B-x is complete), then one
       // bulk reduce-add into Y ----
 #pragma unroll 1
@@ -602,21 +633,6 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
 #pragma unroll
           for (int i1 = 0; i1 < E; ++i1)
             if (i1 < np) tc_store(o + (g * np + i1) * V, ((ok >> i1) & 1u) ? d[g * E + i1] : 0.f);
-        }
-        if (!clean && vok && (wx || wy || wz)) {   // seam nodes lie outside the box: added here
-#pragma unroll
-          for (int g = 0; g < G; ++g) {
-            const int i2 = G * b + g;
-            if (i2 >= np) continue;
-#pragma unroll
-            for (int i1 = 0; i1 < E; ++i1) {
-              if (i1 >= np || !((wx && i1 == P) || (wy && i2 == P) || (wz && i3 == P))) continue;
-              const size_t node = (size_t)node_coord(cx, i1, P, m.Nx, m.periodic) +
-                                  (size_t)m.Nx * (node_coord(cy, i2, P, m.Ny, m.periodic) +
-                                                  (size_t)m.Ny * node_coord(cz, i3, P, m.Nz, m.periodic));
-              tc_atomic_add(Y + node * n_vec + v0 + v, d[g * E + i1]);
-            }
-          }
         }
       }
       fence_async_smem();
