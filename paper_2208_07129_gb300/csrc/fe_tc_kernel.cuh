@@ -107,6 +107,19 @@ __host__ __device__ __forceinline__ int tc_off(int row, int k, int kr) {
   return (row >> 3) * (kr / KC) * 128 + (k / KC) * 128 + (row & 7) * 16 + (k % KC) * ES;
 }
 
+// Line group held by row group R of the F-x and B-x operands.  With four
+// line groups per slow index (H = 4) the groups b = 2, 3 of slow indices
+// 2k and 2k + 1 trade places: the 32 rows of a warp then hold (a, 0), (a, 1),
+// (a ^ 1, 2), (a ^ 1, 3), whose node rows in a cell box start in four
+// different bank groups (a box read or write of one element per row meets
+// no bank conflict), while the packed operand stores of those rows still
+// fill distinct words of one 128-byte core matrix.  The map is its own
+// inverse.
+template <class SH>
+__host__ __device__ __forceinline__ constexpr int tc_lg(int R) {
+  return SH::H == 4 ? (R ^ ((R & 2) ? 4 : 0)) : R;
+}
+
 // G operands packed into one 32-bit word (element k in the low bits).
 template <int KIND>
 __device__ __forceinline__ uint32_t tc_pack1(float x) { return tf32_rna(x); }
@@ -139,7 +152,7 @@ struct TcArgs {
 // Every quantity block starts on a core-matrix boundary (E a multiple of
 // KC), so the address of word (n, qty) is a per-thread base plus a
 // compile-time offset: one packed store per word.
-template <class SH, int NQT, bool SLOWN, int KRN>
+template <class SH, int NQT, bool SLOWN, int KRN, bool PERM = false>
 __device__ __forceinline__ void tc_write_transposed(const float* d, int a, int b, int v, unsigned char* Mb) {
   constexpr int E = SH::E, G = SH::G, H = SH::H, KC = SH::KC, ES = SH::ES;
   constexpr int NL = NQT * E;              // D columns per line = K per line of the next pass
@@ -150,12 +163,16 @@ __device__ __forceinline__ void tc_write_transposed(const float* d, int a, int b
   if (SLOWN) base += (a / G) * RB + ((a % G) * NL / KC) * 128;
   else base += a * H * RB;
   unsigned char* p = Mb + base;
+  // PERM (rows of the next pass placed by tc_lg): row group a H + n / G goes
+  // to the row group of slow index a ^ 1 when (n / G) & 2
+  const int alt = (a & 1) ? -H * RB : H * RB;
 #pragma unroll
   for (int n = 0; n < E; ++n) {
 #pragma unroll
     for (int q = 0; q < NQT; ++q) {
       const int off = SLOWN ? n * H * RB + q * (E / KC) * 128
-                            : (n / G) * RB + ((n % G) * NL / KC) * 128 + q * (E / KC) * 128;
+                            : (n / G) * RB + ((n % G) * NL / KC) * 128 + q * (E / KC) * 128 +
+                                  ((PERM && SH::H == 4 && ((n / G) & 2)) ? alt : 0);
       if constexpr (G * ES == 8) {   // two TF32 operands: one 8-byte store
         *reinterpret_cast<uint2*>(p + off) = make_uint2(tf32_rna(d[q * E + n]), tf32_rna(d[NL + q * E + n]));
       } else {
@@ -444,7 +461,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       }
 #pragma unroll
       for (int j = 0; j < T; ++j) {
-        const int r = j * 128 + lt, L = r >> 3;
+        const int r = j * 128 + lt, L = tc_lg<SH>(r >> 3);
         if (L >= SH::LINES) continue;
         const int i3 = L / H;
         float vals[SH::Kr(0)];
@@ -466,7 +483,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       // load of the thread is issued before the first use ----
 #pragma unroll
       for (int j = 0; j < T; ++j) {
-        const int r = j * 128 + lt, L = r >> 3;
+        const int r = j * 128 + lt, L = tc_lg<SH>(r >> 3);
         if (L >= SH::LINES) continue;
         const int i3 = L / H;
         const int gz = node_coord(cz, i3, P, m.Nz, m.periodic);
@@ -508,6 +525,9 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
 
     FE_TC_ISSUE(0, Sb)
     if constexpr (CVS) {   // F-x has read its operand: the cell's c values take its place
+      // (one 2 KB copy; the four line groups of a warp then read two banks
+      // twice, which costs less than sixteen smaller copies into a skewed
+      // layout did)
       if (lt == 0) {
         mbar_arrive_expect_tx(lbar, (uint32_t)(E * E * E * sizeof(float)));
         bulk_load(Sb, geo.ptC + (size_t)e * (E * E * E), (uint32_t)(E * E * E * sizeof(float)), lbar);
@@ -518,7 +538,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
     for (int j = 0; j < T; ++j) {   // F-x: row (i3, b), lines i2 -> A of F-y: (q1, i3 / G)
       float d[SH::Nr(0)];
       tmem_load<SH::Nr(0)>(tlane + j * SH::Nr(0), d);
-      const int r = j * 128 + lt, L = r >> 3;
+      const int r = j * 128 + lt, L = tc_lg<SH>(r >> 3);
       if (L < SH::LINES) tc_write_transposed<SH, 2, true, SH::Kr(1)>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(1, Mb)
@@ -599,7 +619,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       float d[SH::Nr(4)];
       tmem_load<SH::Nr(4)>(tlane + j * SH::Nr(4), d);
       const int r = j * 128 + lt, L = r >> 3;
-      if (L < SH::LINES) tc_write_transposed<SH, 2, false, SH::Kr(5)>(d, L / H, L % H, r & 7, Mb);
+      if (L < SH::LINES) tc_write_transposed<SH, 2, false, SH::Kr(5), true>(d, L / H, L % H, r & 7, Mb);
     }
     FE_TC_ISSUE(5, Mb)
     if constexpr (TMA) {   // the task thread 0 took, and whether its box is loading
@@ -619,7 +639,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       for (int j = 0; j < T; ++j) {   // B-x: row (i3, b), lines i2 = G b + g, D = [g][i1]
         float d[SH::Nr(5)];
         tmem_load<SH::Nr(5)>(tlane + j * SH::Nr(5), d);
-        const int r = j * 128 + lt, L = r >> 3;
+        const int r = j * 128 + lt, L = tc_lg<SH>(r >> 3);
         if (L >= SH::LINES) continue;
         const int i3 = L / H, b = L % H;
         if (i3 >= np) continue;
@@ -646,7 +666,7 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
       for (int j = 0; j < T; ++j) {   // B-x and assembly: row (i3, b), lines i2 = G b + g, D = [g][i1]
         float d[SH::Nr(5)];
         tmem_load<SH::Nr(5)>(tlane + j * SH::Nr(5), d);
-        const int r = j * 128 + lt, L = r >> 3;
+        const int r = j * 128 + lt, L = tc_lg<SH>(r >> 3);
         if (L >= SH::LINES || !vok) continue;
         const int i3 = L / H;
         if (i3 >= np) continue;
