@@ -335,8 +335,9 @@ def solve_bench(fe, torch, cpu: bool = True, inner_modes=("fp32",)):
     operator) for the block PCG solve of the 24^3, p=6, 128-column problem,
     every solve run to the end on all 128 columns: FP64 Jacobi-PCG with the
     FP64 operator, FP64 Jacobi-PCG with the double-float operator, mixed
-    precision (inner Jacobi-PCG in each of `inner_modes`, FP64 refinement), and
-    the learned preconditioner inside the mixed solve."""
+    precision (inner Jacobi-PCG in each of `inner_modes`, FP64 refinement:
+    FP32 CUDA-core products, TF32 and BF16 tensor-core products), and the
+    learned preconditioner inside the mixed solve."""
     w = inputs.WORKLOADS["c5"]
     ctx = fe.setup_workload(w)
     out = {"workload": w.name, "rtol": 1e-8, "columns": w.n_vec}
@@ -862,7 +863,7 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and not args.no_solve:
-        out["pcg"] = solve_bench(fe, torch, cpu=not args.no_cpu)
+        out["pcg"] = solve_bench(fe, torch, cpu=not args.no_cpu, inner_modes=("fp32", "tf32", "bf16"))
     if rank == 0 and not args.no_batch:
         out["batch"] = batch_bench(fe, torch)
     if rank == 0 and not args.no_distorted:
