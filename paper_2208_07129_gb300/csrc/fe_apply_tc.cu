@@ -16,6 +16,8 @@ namespace fe {
 namespace {
 
 constexpr int kTcQueues = 32;   // at least the largest colour count (27)
+static_assert(kTcCvBytes == kTcCvWords * 4 && tc_cv_index(7, 7, 7) < kTcCvWords,
+              "the staged c block built at setup is the one the kernel copies");
 
 using Shape8TF32 = TcShape<8, 2, kTcTF32>;
 using Shape8BF16 = TcShape<8, 2, kTcBF16>;
@@ -157,7 +159,8 @@ cudaError_t launch_tc(const fe_ctx* c, const unsigned char* img, const TIO* X, T
   if (TMA && (e = cudaMemsetAsync(Y, 0, c->n_dofs * (size_t)n_vec * sizeof(TIO), s)) != cudaSuccess) return e;
   if (TMA && (e = cudaMemsetAsync(c->d_tcq, 0, kTcQueues * sizeof(int), s)) != cudaSuccess) return e;
   const Geom<float> geo = make_geom<float>(c);
-  TcArgs a{img, nullptr, c->np, c->nq, c->d_status, nullptr};
+  TcArgs a{img, nullptr, c->np, c->nq, c->d_status, nullptr, c->d_ptCtc};
+  if (QF && TMA && c->d_ptCtc == nullptr) return cudaErrorInvalidValue;
   const int n_vb = (n_vec + kTcVectors - 1) / kTcVectors;
   if (TMA && c->colors.n_colors > kTcQueues) return cudaErrorInvalidValue;
   for (int k = 0; k < c->colors.n_colors; ++k) {

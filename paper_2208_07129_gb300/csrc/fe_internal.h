@@ -95,6 +95,9 @@ struct KernelLaunch {
 
 }  // namespace fe
 
+// Floats per cell of fe_ctx::d_ptCtc: 8 planes of 72 (64 values, 8 of padding).
+constexpr int kTcCvWords = 8 * 72;
+
 struct fe_ctx {
   // mesh and discretisation
   int nx, ny, nz, periodic, p, np, nq, quad_kind;
@@ -115,6 +118,9 @@ struct fe_ctx {
   int* d_cells = nullptr;
   double *d_cellG64 = nullptr, *d_ptG64 = nullptr, *d_ptC64 = nullptr;
   float *d_cellG32 = nullptr, *d_ptG32 = nullptr, *d_ptC32 = nullptr;
+  // n_q = 8 (tcgen05 kernel): the same FP32 c values per cell in the layout
+  // the kernel stages them in (kTcCvWords floats per cell, see fe_setup.cu)
+  float* d_ptCtc = nullptr;
   fe::ff *d_cellGff = nullptr, *d_ptGff = nullptr, *d_ptCff = nullptr;   // double-float copies
   double* d_detJ = nullptr;
   int* d_status = nullptr;

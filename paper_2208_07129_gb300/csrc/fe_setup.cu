@@ -207,6 +207,20 @@ cudaError_t upload_point_coeff(fe_ctx* c, const std::vector<double>& ptC) {
   cudaError_t e = upload(&c->d_ptC64, ptC.data(), ptC.size());
   if (e == cudaSuccess) e = upload_as_float(&c->d_ptC32, ptC);
   if (e == cudaSuccess) e = upload_as_ff(&c->d_ptCff, ptC);
+  // tcgen05 kernel, n_q = 8: per cell, plane q3 at a pitch of 72 floats and
+  // its rows q2 >= 4 shifted by 4, so that the kernel's one bulk copy per
+  // cell lands in a layout whose reads meet no bank conflict
+  cudaFree(c->d_ptCtc);
+  c->d_ptCtc = nullptr;
+  if (e == cudaSuccess && !c->refined && c->nq == 8) {
+    std::vector<double> skew(c->n_cells * (size_t)kTcCvWords, 0.0);
+    for (size_t k = 0; k < c->n_cells; ++k)
+      for (int q3 = 0; q3 < 8; ++q3)
+        for (int q2 = 0; q2 < 8; ++q2)
+          for (int q1 = 0; q1 < 8; ++q1)
+            skew[k * kTcCvWords + 72 * q3 + 8 * q2 + (q2 >= 4 ? 4 : 0) + q1] = ptC[k * 512 + 64 * q3 + 8 * q2 + q1];
+    e = upload_as_float(&c->d_ptCtc, skew);
+  }
   return e;
 }
 
@@ -392,7 +406,7 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
 extern "C" void fe_destroy(fe_ctx* c) {
   if (!c) return;
   cudaFree(c->d_cells); cudaFree(c->d_cellG64); cudaFree(c->d_ptG64); cudaFree(c->d_ptC64);
-  cudaFree(c->d_cellG32); cudaFree(c->d_ptG32); cudaFree(c->d_ptC32); cudaFree(c->d_detJ);
+  cudaFree(c->d_cellG32); cudaFree(c->d_ptG32); cudaFree(c->d_ptC32); cudaFree(c->d_ptCtc); cudaFree(c->d_detJ);
   cudaFree(c->d_cellGff); cudaFree(c->d_ptGff); cudaFree(c->d_ptCff);
   cudaFree(c->d_status); cudaFree(c->d_stage);
   cudaFree(c->d_tcimg[0]); cudaFree(c->d_tcimg[1]); cudaFree(c->d_tcmask); cudaFree(c->d_tcq); cudaFree(c->d_small);

@@ -143,7 +143,16 @@ struct TcArgs {
   int np, nq;
   int* status;                 // FE_ETIMEOUT is raised here when a bounded wait gives up
   int* queue;                  // TMA kernels: task counter of the launch (zero at launch)
+  const float* cvs;            // n_q = 8: c values per cell in the staged layout (tc_cv_index)
 };
+
+// Word of c at point (q1, q2, q3) in a cell's staged block (n_q = 8): plane
+// q3 at a pitch of 72 floats, rows q2 >= 4 shifted by 4, so that the four
+// line groups of a warp (q2 = 2b + g) read four different banks.
+__host__ __device__ __forceinline__ constexpr int tc_cv_index(int q1, int q2, int q3) {
+  return 72 * q3 + 8 * q2 + (q2 >= 4 ? 4 : 0) + q1;
+}
+constexpr int kTcCvBytes = 8 * 72 * 4;
 
 // Transposed write of one row of D (pass S) into the A layout of pass S + 1.
 // The row's line group has slow coordinate `a` and lines f = G b + g; D
@@ -525,12 +534,9 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
 
     FE_TC_ISSUE(0, Sb)
     if constexpr (CVS) {   // F-x has read its operand: the cell's c values take its place
-      // (one 2 KB copy; the four line groups of a warp then read two banks
-      // twice, which costs less than sixteen smaller copies into a skewed
-      // layout did)
       if (lt == 0) {
-        mbar_arrive_expect_tx(lbar, (uint32_t)(E * E * E * sizeof(float)));
-        bulk_load(Sb, geo.ptC + (size_t)e * (E * E * E), (uint32_t)(E * E * E * sizeof(float)), lbar);
+        mbar_arrive_expect_tx(lbar, (uint32_t)kTcCvBytes);
+        bulk_load(Sb, args.cvs + (size_t)e * (kTcCvBytes / 4), (uint32_t)kTcCvBytes, lbar);
       }
       load_pending = true;
     }
@@ -568,14 +574,14 @@ __global__ void __launch_bounds__(128 * TcShape<E, G, KIND>::SLOTS, 1)
         // points (q1, q2, q3) of this line: q3 < nq exist when the line does
         // (values at padded points meet zero B entries in B-z)
         const bool line = QF || (q1 < nq && q2 < nq);
-        const float* pc = CVS ? reinterpret_cast<const float*>(Sb) + q1 + E * q2
+        const float* pc = CVS ? reinterpret_cast<const float*>(Sb) + tc_cv_index(q1, q2, 0)
                               : geo.ptC + (size_t)e * nq3 + q1 + nq * q2;
         const float* pg0 = GEN ? geo.ptG + (size_t)e * 6 * nq3 + q1 + nq * q2 : nullptr;
 #pragma unroll
         for (int q3 = 0; q3 < E; ++q3) {
           float cv = 0.f;
           if (QF || (line && q3 < nq)) {
-            cv = CVS ? pc[q3 * E * E] : __ldg(pc + q3 * nq2);
+            cv = CVS ? pc[tc_cv_index(0, 0, q3)] : __ldg(pc + q3 * nq2);
             if (GEN) {
               const float* pg = pg0 + q3 * nq2;
               const float g00 = __ldg(pg), g01 = __ldg(pg + nq3), g02 = __ldg(pg + 2 * nq3);
