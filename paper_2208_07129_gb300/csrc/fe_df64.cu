@@ -1,28 +1,24 @@
-// FE_DF64 instantiations of the double-float cell kernel on structured meshes.
-#include "fe_ff_body.cuh"
+// FE_DF64 entry points of the double-float cell kernel on structured meshes;
+// the kernels themselves are instantiated in fe_df64_{affine,general}.cu and
+// fe_df64_scaled_{affine,general}.cu.
+#include "fe_internal.h"
 
 namespace fe {
 
+template <bool GEN, bool SC>
+cudaError_t apply_df64_variant(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s,
+                               const Scale<double>& sc);
+
 cudaError_t apply_df64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s) {
   const Scale<double> none{};
-#define FE_CASE(P, NQ)                                                                  \
-  if (c->p == P && c->nq == NQ)                                                         \
-    return c->general ? launch_df64<P + 1, NQ, true, false>(c, X, Y, n_vec, s, none)   \
-                      : launch_df64<P + 1, NQ, false, false>(c, X, Y, n_vec, s, none);
-  FE_FOR_EACH_P_NQ(FE_CASE)
-#undef FE_CASE
-  return cudaErrorInvalidValue;
+  return c->general ? apply_df64_variant<true, false>(c, X, Y, n_vec, s, none)
+                    : apply_df64_variant<false, false>(c, X, Y, n_vec, s, none);
 }
 
 cudaError_t apply_scaled_df64(const fe_ctx* c, const double* X, double* Y, int n_vec, const Scale<double>& sc,
                               cudaStream_t s) {
-#define FE_CASE(P, NQ)                                                                \
-  if (c->p == P && c->nq == NQ)                                                       \
-    return c->general ? launch_df64<P + 1, NQ, true, true>(c, X, Y, n_vec, s, sc)    \
-                      : launch_df64<P + 1, NQ, false, true>(c, X, Y, n_vec, s, sc);
-  FE_FOR_EACH_P_NQ(FE_CASE)
-#undef FE_CASE
-  return cudaErrorInvalidValue;
+  return c->general ? apply_df64_variant<true, true>(c, X, Y, n_vec, s, sc)
+                    : apply_df64_variant<false, true>(c, X, Y, n_vec, s, sc);
 }
 
 }  // namespace fe
