@@ -298,6 +298,14 @@ fe_status fe_last_device_status(fe_ctx* ctx);
 
 const char* fe_status_str(fe_status s);
 
+/* Name of the CUDA runtime error (cudaGetErrorName, e.g.
+ * "cudaErrorInvalidValue") behind the most recent FE_ECUDA or FE_ENOMEM that
+ * any call of this library returned on the calling host thread, followed by
+ * the step that met it where the library names one ("... in <step>"), or
+ * "none".  Reading it does not clear it; the string belongs to the library
+ * and stays valid until the thread's next failing call. */
+const char* fe_last_cuda_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,8 @@ typedef struct {
   int val_jacobi_iterations; /* FP32 PCG iterations to 1e-7 on the held-out columns, Jacobi */
   int val_learned_iterations;/* the same with the kept checkpoint (the Jacobi count when none beat it) */
   int best_epoch;            /* epoch of the kept checkpoint; 0 = zero output layer (Jacobi) */
+  float val_loss_jacobi;     /* training objective on the held-out snapshots, Jacobi (zero output layer) */
+  float val_loss_kept;       /* the same for the kept network */
 } fe_train_info;
 
 /* Random initial weights (W1 ~ U(+-1/sqrt(n3)), W2 ~ U(+-1e-3/sqrt(128)),
@@ -80,12 +82,17 @@ fe_status fe_precond_init(fe_ctx* ctx, unsigned long long seed);
  *  FE_TRAIN_OPERATOR_RESIDUAL: one snapshot r_k per step, loss
  *    mean (A z(r_k) - r_k)^2 over all cells' patches at once (two FP32
  *    operator applications per step: A z and the gradient A (A z - r));
- *  With n_val > 0 (operator objectives), after every epoch an FP32 block
- *  PCG on n_val held-out random right-hand sides counts iterations to 1e-7
- *  with the current network; the weights of the best epoch are kept, where
- *  "epoch 0" is the network with its output layer set to zero, i.e. exactly
- *  Jacobi -- so the kept network never needs more validation iterations
- *  than Jacobi.
+ *  With n_val > 0 (operator objectives), n_val held-out random right-hand
+ *  sides are solved once by FP32 Jacobi-PCG to 1e-7 (its iteration count and
+ *  solution x*), recording up to four held-out snapshots spread over the
+ *  iterations the training snapshots span.  After every epoch the objective
+ *  is evaluated on those snapshots; "epoch 0" is the network with its output
+ *  layer set to zero, i.e. exactly Jacobi.  The epoch of the lowest held-out
+ *  loss (when it is not epoch 0) and the last epoch are then tried, in that
+ *  order, by one FP32 PCG solve of the held-out right-hand sides each: the
+ *  first that needs fewer iterations than Jacobi is kept, otherwise the
+ *  output layer is set to zero (Jacobi).  The kept network never needs more
+ *  validation iterations than Jacobi.
  *  FE_TRAIN_PATCH_ERROR: inputs R_e r_k / s_e, targets
  *    HF(R_e(x* - x_k - D^-1 r_k)) / s_e, HF subtracting the trilinear
  *    interpolant of the patch's eight corner values, mini-batches of `batch`

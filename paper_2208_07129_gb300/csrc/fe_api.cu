@@ -7,7 +7,7 @@ using namespace fe;
 
 namespace {
 fe_status from_cuda(cudaError_t e) {
-  return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
+  return fe::cuda_status(e);
 }
 size_t elem_size(fe_mode m) {
   return (m == FE_FP64 || m == FE_DF64) ? sizeof(double) : m == FE_BF16S ? (size_t)2 : sizeof(float);

@@ -209,6 +209,7 @@ struct fe_batch {
   void** d_ptrs = nullptr;
   size_t smem = 0;
   int grid = 0;
+  int grid_kind[kKinds] = {0};         // persistent grid of each degree's kernel (per-degree kernels)
   cudaStream_t cap = nullptr;
   cudaStream_t side[kKinds] = {};       // one capture branch per degree
   cudaEvent_t fork = nullptr, join[kKinds] = {};
@@ -220,7 +221,7 @@ struct fe_batch {
 namespace {
 
 fe_status from_cuda(cudaError_t e) {
-  return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
+  return fe::cuda_status(e);
 }
 
 template <typename T>
@@ -295,8 +296,23 @@ int autotune(const fe_ctx* c, int n_vec_full, fe_mode mode, float* spent_ms) {
   return best;
 }
 
-// Capture the persistent kernel of one degree: grid = its occupancy x SMs
-// (at most one CTA per work item).
+// The persistent kernel of one degree: before the capture, its shared-memory
+// attribute and its grid = occupancy x SMs (at most one CTA per work item);
+// then its launch, recorded into the graph.
+template <typename T, int NP, int NQ>
+cudaError_t prepare_kind(fe_batch* b, int kind, int n_k, size_t smem) {
+  auto kern = batch_kernel<T, NP, NQ>;
+  cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
+  int per_sm = 0, sms = 0, dev = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  b->grid_kind[kind] = std::max(1, std::min(n_k, std::max(1, per_sm) * sms));
+  b->grid = std::max(b->grid, b->grid_kind[kind]);
+  return cudaSuccess;
+}
+
 template <typename T, int NP, int NQ>
 cudaError_t launch_kind(fe_batch* b, int kind, int n_k, size_t smem) {
   auto kern = batch_kernel<T, NP, NQ>;
@@ -305,19 +321,24 @@ cudaError_t launch_kind(fe_batch* b, int kind, int n_k, size_t smem) {
     if (kind_of(b->ctxs[i]->p) == kind) c0 = b->ctxs[i];
   if (!c0) return cudaErrorInvalidValue;
   const EOTables<T, NP, NQ> tab = make_eotables<T, NP, NQ>(c0);
-  cudaError_t e = cudaSuccess;
-  if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0, sms = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
-  if (e != cudaSuccess) return e;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  const int grid = std::max(1, std::min(n_k, std::max(1, per_sm) * sms));
-  b->grid = std::max(b->grid, grid);
-  kern<<<grid, kBatchThreads, smem, b->side[kind]>>>(tab, static_cast<const BatchProblemDev<T>*>(b->d_probs),
-                                              const_cast<const void* const*>(b->d_ptrs),
-                                              b->d_items + b->item_begin[kind], n_k, b->d_next + kind, b->d_done,
-                                              b->d_need, b->d_status, b->d_wait_ns);
+  kern<<<b->grid_kind[kind], kBatchThreads, smem, b->side[kind]>>>(
+      tab, static_cast<const BatchProblemDev<T>*>(b->d_probs), const_cast<const void* const*>(b->d_ptrs),
+      b->d_items + b->item_begin[kind], n_k, b->d_next + kind, b->d_done, b->d_need, b->d_status, b->d_wait_ns);
   return cudaGetLastError();
+}
+
+// Both steps for kind k (p = k + 3, n_q = p + 2).
+template <typename T>
+cudaError_t for_kind(fe_batch* b, int kind, int n_k, size_t smem, bool launch) {
+  switch (kind) {
+    case 0: return launch ? launch_kind<T, 4, 5>(b, kind, n_k, smem) : prepare_kind<T, 4, 5>(b, kind, n_k, smem);
+    case 1: return launch ? launch_kind<T, 5, 6>(b, kind, n_k, smem) : prepare_kind<T, 5, 6>(b, kind, n_k, smem);
+    case 2: return launch ? launch_kind<T, 6, 7>(b, kind, n_k, smem) : prepare_kind<T, 6, 7>(b, kind, n_k, smem);
+    case 3: return launch ? launch_kind<T, 7, 8>(b, kind, n_k, smem) : prepare_kind<T, 7, 8>(b, kind, n_k, smem);
+    case 4: return launch ? launch_kind<T, 8, 9>(b, kind, n_k, smem) : prepare_kind<T, 8, 9>(b, kind, n_k, smem);
+    case 5: return launch ? launch_kind<T, 9, 10>(b, kind, n_k, smem) : prepare_kind<T, 9, 10>(b, kind, n_k, smem);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>
@@ -400,6 +421,7 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
   b->n_items = (int)items.size();
   b->n_phases = phases;
   b->smem = smem;
+  const char* where = "fe_batch_create: device tables";
   cudaError_t e = cudaMalloc(&b->d_probs, n * sizeof(BatchProblemDev<T>));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_probs, hp.data(), n * sizeof(BatchProblemDev<T>), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_items, std::max<size_t>(1, items.size()) * sizeof(WorkItem));
@@ -419,58 +441,72 @@ fe_status build_batch(fe_batch* b, int autotune_on) {
   b->need = need;
   if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, 2 * n * sizeof(void*));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_ptrs, 2 * n * sizeof(void*));
-  if (e != cudaSuccess) return from_cuda(e);
+  if (e != cudaSuccess) return fe::cuda_status(e, where);
   // graph: reset the queues and the colour counters, then one persistent
   // kernel per degree present, as parallel branches (the degrees share the
   // GPU, and one degree's tail overlaps the others' work).  Every wait of a
   // CTA is on items its own kernel dequeued earlier, whose CTAs are running,
   // so concurrent branches cannot block each other.
+  // kernel attributes and grids first: the capture below only records work
+  where = "fe_batch_create: kernel attributes and grids";
+  if constexpr (merged) {
+    auto kern = batch_kernel_all<T>;
+    e = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
+    int per_sm = 0, sms = 0, dev = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = std::max(1, std::min(b->n_items, std::max(1, per_sm) * sms));
+  } else {
+    for (int kind = 0; kind < kKinds && e == cudaSuccess; ++kind) {
+      const int n_k = b->item_begin[kind + 1] - b->item_begin[kind];
+      if (n_k > 0) e = for_kind<T>(b, kind, n_k, smem, false);
+    }
+  }
+  if (e != cudaSuccess) return fe::cuda_status(e, where);
+  where = "fe_batch_create: streams and events";
   e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   for (int k = 0; k < kKinds && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   for (int k = 0; k < kKinds && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
+    where = "fe_batch_create: captured launches";
     cudaMemsetAsync(b->d_next, 0, kKinds * sizeof(int), b->cap);
     cudaMemsetAsync(b->d_done, 0, need.size() * sizeof(int), b->cap);
     cudaEventRecord(b->fork, b->cap);
     if constexpr (merged) {
-      auto kern = batch_kernel_all<T>;
-      if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      int per_sm = 0, sms = 0;
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-      b->grid = std::max(1, std::min(b->n_items, std::max(1, per_sm) * sms));
-      if (e == cudaSuccess)
-        kern<<<b->grid, kBatchThreads, smem, b->cap>>>(static_cast<const BatchProblemDev<T>*>(b->d_probs),
-                                                       const_cast<const void* const*>(b->d_ptrs), b->d_items,
-                                                       b->n_items, b->d_next, b->d_done, b->d_need, b->d_status,
-                                                       b->d_wait_ns);
+      batch_kernel_all<T><<<b->grid, kBatchThreads, smem, b->cap>>>(
+          static_cast<const BatchProblemDev<T>*>(b->d_probs), const_cast<const void* const*>(b->d_ptrs), b->d_items,
+          b->n_items, b->d_next, b->d_done, b->d_need, b->d_status, b->d_wait_ns);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      e = cudaGetLastError();
+      if (e != cudaSuccess) where = "fe_batch_create: captured resets of the queues";
     }
     for (int kind = 0; kind < kKinds && e == cudaSuccess && !merged; ++kind) {
       const int n_k = b->item_begin[kind + 1] - b->item_begin[kind];
       if (n_k == 0) continue;
       e = cudaStreamWaitEvent(b->side[kind], b->fork, 0);
-      if (e != cudaSuccess) break;
-      switch (kind) {
-        case 0: e = launch_kind<T, 4, 5>(b, kind, n_k, smem); break;
-        case 1: e = launch_kind<T, 5, 6>(b, kind, n_k, smem); break;
-        case 2: e = launch_kind<T, 6, 7>(b, kind, n_k, smem); break;
-        case 3: e = launch_kind<T, 7, 8>(b, kind, n_k, smem); break;
-        case 4: e = launch_kind<T, 8, 9>(b, kind, n_k, smem); break;
-        case 5: e = launch_kind<T, 9, 10>(b, kind, n_k, smem); break;
-        default: break;
-      }
-      if (e == cudaSuccess) e = cudaEventRecord(b->join[kind], b->side[kind]);
+      if (e != cudaSuccess) { where = "fe_batch_create: fork of a degree's branch"; break; }
+      e = for_kind<T>(b, kind, n_k, smem, true);
+      if (e != cudaSuccess) { where = "fe_batch_create: captured launch of a degree's kernel"; break; }
+      e = cudaEventRecord(b->join[kind], b->side[kind]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[kind], 0);
+      if (e != cudaSuccess) where = "fe_batch_create: join of a degree's branch";
     }
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     b->graph = g;
+    if (e == cudaSuccess && e2 != cudaSuccess) where = "fe_batch_create: end of capture";
     if (e == cudaSuccess) e = e2;
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-  return from_cuda(e);
+  if (e == cudaSuccess) {
+    where = "fe_batch_create: graph instantiation";
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  }
+  return fe::cuda_status(e, where);
 }
 
 }  // namespace

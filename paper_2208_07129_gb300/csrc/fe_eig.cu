@@ -25,7 +25,7 @@ using namespace fe;
 namespace {
 
 fe_status from_cuda(cudaError_t e) {
-  return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
+  return fe::cuda_status(e);
 }
 
 bool overlaps(const void* a, const void* b, size_t bytes) {

@@ -147,10 +147,12 @@ __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, con
   }
   __syncthreads();
   // ---- z-lines: gradient along z, quadrature-point operation, transposed z pass ----
+  // Cells without per-point geometry are axis-aligned boxes (checked at
+  // setup): their metric is diagonal, and the point operation scales each
+  // gradient component by one coefficient.
   T g00, g01, g02, g11, g12, g22;
   if (!GEN) {
-    g00 = geo.cellG[e * 6 + 0]; g01 = geo.cellG[e * 6 + 1]; g02 = geo.cellG[e * 6 + 2];
-    g11 = geo.cellG[e * 6 + 3]; g12 = geo.cellG[e * 6 + 4]; g22 = geo.cellG[e * 6 + 5];
+    g00 = geo.cellG[e * 6 + 0]; g11 = geo.cellG[e * 6 + 3]; g22 = geo.cellG[e * 6 + 5];
   }
   const T* ptC = geo.ptC + (size_t)e * NQ3;
   for (int l = ty; l < NQ * NQ; l += nty) {
@@ -166,10 +168,14 @@ __device__ __forceinline__ void cell_body_eo(const EOTables<T, NP, NQ>& tab, con
       if (GEN) {
         const T* pg = geo.ptG + (size_t)e * 6 * NQ3 + Q;
         g00 = pg[0]; g01 = pg[NQ3]; g02 = pg[2 * NQ3]; g11 = pg[3 * NQ3]; g12 = pg[4 * NQ3]; g22 = pg[5 * NQ3];
+        S0[Q * B + v] = g00 * d0 + g01 * d1 + g02 * d2;
+        S1[Q * B + v] = g01 * d0 + g11 * d1 + g12 * d2;
+        h2[q] = g02 * d0 + g12 * d1 + g22 * d2;
+      } else {
+        S0[Q * B + v] = g00 * d0;
+        S1[Q * B + v] = g11 * d1;
+        h2[q] = g22 * d2;
       }
-      S0[Q * B + v] = g00 * d0 + g01 * d1 + g02 * d2;
-      S1[Q * B + v] = g01 * d0 + g11 * d1 + g12 * d2;
-      h2[q] = g02 * d0 + g12 * d1 + g22 * d2;
       t[q] = ptC[Q] * t[q];
     }
     eo_apply<T, NQ, NQ, -1>(tab.Dt, h2, o);

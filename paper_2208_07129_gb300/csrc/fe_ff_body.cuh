@@ -130,10 +130,10 @@ __device__ __forceinline__ void cell_body_ff(const EOTables<ff, NP, NQ>& tab, co
   }
   __syncthreads();
   // ---- z-lines: gradient along z, quadrature-point operation, transposed z pass ----
+  // cells without per-point geometry are axis-aligned boxes: diagonal metric
   ff g00, g01, g02, g11, g12, g22;
   if (!GEN) {
-    g00 = geo.cellG[e * 6 + 0]; g01 = geo.cellG[e * 6 + 1]; g02 = geo.cellG[e * 6 + 2];
-    g11 = geo.cellG[e * 6 + 3]; g12 = geo.cellG[e * 6 + 4]; g22 = geo.cellG[e * 6 + 5];
+    g00 = geo.cellG[e * 6 + 0]; g11 = geo.cellG[e * 6 + 3]; g22 = geo.cellG[e * 6 + 5];
   }
   const ff* ptC = geo.ptC + (size_t)e * NQ3;
   for (int l = ty; l < NQ * NQ; l += nty) {
@@ -149,14 +149,18 @@ __device__ __forceinline__ void cell_body_ff(const EOTables<ff, NP, NQ>& tab, co
       if (GEN) {
         const ff* pg = geo.ptG + (size_t)e * 6 * NQ3 + Q;
         g00 = pg[0]; g01 = pg[NQ3]; g02 = pg[2 * NQ3]; g11 = pg[3 * NQ3]; g12 = pg[4 * NQ3]; g22 = pg[5 * NQ3];
+        ffacc r0 = acc_first(g00, d0), r1 = acc_first(g01, d0), r2 = acc_first(g02, d0);
+        acc_fma(r0, g01, d1); acc_fma(r0, g02, d2);
+        acc_fma(r1, g11, d1); acc_fma(r1, g12, d2);
+        acc_fma(r2, g12, d1); acc_fma(r2, g22, d2);
+        S0[Q * B + v] = acc_value(r0);
+        S1[Q * B + v] = acc_value(r1);
+        h2[q] = acc_value(r2);
+      } else {
+        S0[Q * B + v] = ff_mul(g00, d0);
+        S1[Q * B + v] = ff_mul(g11, d1);
+        h2[q] = ff_mul(g22, d2);
       }
-      ffacc r0 = acc_first(g00, d0), r1 = acc_first(g01, d0), r2 = acc_first(g02, d0);
-      acc_fma(r0, g01, d1); acc_fma(r0, g02, d2);
-      acc_fma(r1, g11, d1); acc_fma(r1, g12, d2);
-      acc_fma(r2, g12, d1); acc_fma(r2, g22, d2);
-      S0[Q * B + v] = acc_value(r0);
-      S1[Q * B + v] = acc_value(r1);
-      h2[q] = acc_value(r2);
       t[q] = ff_mul(ptC[Q], t[q]);
     }
     eo_apply_ff<NQ, NQ, -1>(tab.Dt, h2, o);

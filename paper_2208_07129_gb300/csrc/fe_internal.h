@@ -42,7 +42,9 @@ struct Tables {
 
 // Geometry of the quadrature-point operation.  With weights folded into the
 // tables:  G_sd = mu det J (J^-1 J^-T)_sd   and   c = det J V.
-// Affine cells: one G per cell (cellG[e*6 + k], k = 00,01,02,11,12,22).
+// Affine cells (axis-aligned boxes): one G per cell (cellG[e*6 + k],
+// k = 00,01,02,11,12,22), diagonal: the even-odd and double-float bodies
+// read only k = 00, 11, 22.
 // General (trilinear) cells: ptG[(e*6 + k) * nq3 + Q].  Always ptC[e*nq3 + Q].
 template <typename T>
 struct Geom {
@@ -186,6 +188,11 @@ namespace fe {
 // device, so the highest value set is remembered per (kernel, device); the
 // cache is guarded by a mutex, so host threads may launch concurrently.
 cudaError_t ensure_dyn_smem(const void* kern, size_t smem);
+// Status of a CUDA runtime result (FE_OK, FE_ENOMEM or FE_ECUDA); a failure
+// is also recorded as the calling host thread's last CUDA error, with the
+// step that met it when `where` (a static string) is given, which
+// fe_last_cuda_error() reports.
+fe_status cuda_status(cudaError_t e, const char* where = nullptr);
 // Kernel dispatch (defined in the kernel translation units).
 cudaError_t apply_cc_f64(const fe_ctx* c, const double* X, double* Y, int n_vec, cudaStream_t s);
 cudaError_t apply_cc_f32(const fe_ctx* c, const float* X, float* Y, int n_vec, cudaStream_t s);

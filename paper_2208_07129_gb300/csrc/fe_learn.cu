@@ -292,21 +292,25 @@ __global__ void build_images_kernel(const float* W1, const float* W2, __nv_bfloa
 // ---------------------------------------------------------------------------
 
 // C[m][n] = sum_k A(m,k) B(k,n), A(m,k) = A[m sam + k sak], B(k,n) = B[k sbk + n sbn], C row-major ldc.
+// blockIdx.z takes the slice [z kchunk, (z + 1) kchunk) of k and writes its
+// partial product to C + z c_slice (one slice: the whole product).
 __global__ void __launch_bounds__(256) sgemm_strided(int M, int N, int K, const float* __restrict__ A, long sam,
                                                      long sak, const float* __restrict__ B, long sbk, long sbn,
-                                                     float* __restrict__ C, int ldc) {
+                                                     float* __restrict__ C, int ldc, int kchunk, size_t c_slice) {
   __shared__ float As[16][64 + 1];
   __shared__ float Bs[16][64 + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  C += blockIdx.z * c_slice;
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  for (int k0 = kb; k0 < ke; k0 += 16) {
     for (int l = threadIdx.x; l < 16 * 64; l += 256) {
       const int kk = l / 64, mm = l % 64;
       const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : 0.f;
+      As[kk][mm] = (gm < M && gk < ke) ? A[gm * sam + gk * sak] : 0.f;
       const int gn = n0 + mm;
-      Bs[kk][mm] = (gn < N && gk < K) ? B[gk * sbk + gn * sbn] : 0.f;
+      Bs[kk][mm] = (gn < N && gk < ke) ? B[gk * sbk + gn * sbn] : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -332,10 +336,36 @@ __global__ void __launch_bounds__(256) sgemm_strided(int M, int N, int K, const 
     }
 }
 
+// C[i] = sum over the S slices of part[z][i], in slice order (deterministic).
+__global__ void sum_slices_kernel(const float* __restrict__ part, int S, size_t n, float* __restrict__ C) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int z = 0; z < S; ++z) acc += part[z * n + i];
+    C[i] = acc;
+  }
+}
+
+constexpr int kMaxSlices = 32;   // slices of k of a split product (part holds kMaxSlices x M x N)
+
+// C = A B (M x N, row-major).  A product with few 64 x 64 output tiles and a
+// long k (the weight gradients: k runs over every patch of a snapshot) is
+// split into slices of k, so that about two CTAs per SM work on it, when a
+// slice buffer `part` is given; the slices are then summed in order.
 static cudaError_t gemm(int M, int N, int K, const float* A, long sam, long sak, const float* B, long sbk, long sbn,
-                        float* C, cudaStream_t s) {
+                        float* C, cudaStream_t s, float* part = nullptr) {
   dim3 grid((N + 63) / 64, (M + 63) / 64);
-  sgemm_strided<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, N);
+  const int tiles = (int)(grid.x * grid.y);
+  int S = 1;
+  if (part && tiles < 152) S = std::min(std::min(kMaxSlices, (2 * 152 + tiles - 1) / tiles), std::max(1, K / 1024));
+  if (S <= 1) {
+    sgemm_strided<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, N, K, 0);
+    return cudaGetLastError();
+  }
+  const int kc = ((K + S - 1) / S + 15) / 16 * 16;
+  grid.z = (K + kc - 1) / kc;
+  const size_t mn = (size_t)M * N;
+  sgemm_strided<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, part, N, kc, mn);
+  sum_slices_kernel<<<(unsigned)std::min<size_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, (int)grid.z, mn, C);
   return cudaGetLastError();
 }
 
@@ -669,7 +699,7 @@ static unsigned grid_for(size_t total) {
 // ---------------------------------------------------------------------------
 
 static fe_status from_cuda(cudaError_t e) {
-  return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
+  return fe::cuda_status(e);
 }
 
 static size_t smem_bytes(int K1) {
@@ -760,19 +790,21 @@ fe_status learned_precond_apply(fe_ctx* c, const void* r, void* z, int nv, bool 
 struct TrainBufs {
   float *Hpre = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr;
   float *gW1 = nullptr, *gb1 = nullptr, *gW2 = nullptr, *gb2 = nullptr, *partial = nullptr, *loss = nullptr;
+  float* slices = nullptr;   // k slices of the weight-gradient products
 };
 
 static cudaError_t alloc_train(TrainBufs& b, int rows, int n3) {
   cudaError_t e = cudaSuccess;
   const size_t sizes[] = {(size_t)rows * kHidden, (size_t)rows * n3, (size_t)rows * n3, (size_t)rows * kHidden,
-                          (size_t)kHidden * n3, (size_t)kHidden, (size_t)n3 * kHidden, (size_t)n3, 2048, 1};
-  float** ptrs[] = {&b.Hpre, &b.Y, &b.dY, &b.dH, &b.gW1, &b.gb1, &b.gW2, &b.gb2, &b.partial, &b.loss};
-  for (int k = 0; k < 10 && e == cudaSuccess; ++k) e = cudaMalloc(ptrs[k], sizes[k] * sizeof(float));
+                          (size_t)kHidden * n3, (size_t)kHidden, (size_t)n3 * kHidden, (size_t)n3, 2048, 1,
+                          (size_t)kMaxSlices * kHidden * n3};
+  float** ptrs[] = {&b.Hpre, &b.Y, &b.dY, &b.dH, &b.gW1, &b.gb1, &b.gW2, &b.gb2, &b.partial, &b.loss, &b.slices};
+  for (int k = 0; k < 11 && e == cudaSuccess; ++k) e = cudaMalloc(ptrs[k], sizes[k] * sizeof(float));
   return e;
 }
 
 static void free_train(TrainBufs& b) {
-  for (float* p : {b.Hpre, b.Y, b.dY, b.dH, b.gW1, b.gb1, b.gW2, b.gb2, b.partial, b.loss}) cudaFree(p);
+  for (float* p : {b.Hpre, b.Y, b.dY, b.dH, b.gW1, b.gb1, b.gW2, b.gb2, b.partial, b.loss, b.slices}) cudaFree(p);
 }
 
 // Forward and backward of the MSE loss for a batch; gradients into b.g*.
@@ -791,13 +823,13 @@ static cudaError_t forward_backward(LearnedPrecond* L, TrainBufs& b, const float
   mse_grad_kernel<<<nb, 256, 0, s>>>(b.Y, T, b.dY, tot, 1.0f / (float)tot, b.partial);
   sum_kernel<<<1, 32, 0, s>>>(b.partial, nb, 1.0f / (float)tot, b.loss);
   // dW2 = dY^T H ; db2 = colsum dY
-  if ((e = gemm(n3, H, rows, b.dY, 1, n3, b.Hpre, H, 1, b.gW2, s)) != cudaSuccess) return e;
+  if ((e = gemm(n3, H, rows, b.dY, 1, n3, b.Hpre, H, 1, b.gW2, s, b.slices)) != cudaSuccess) return e;
   colsum_kernel<<<(n3 + 127) / 128, 128, 0, s>>>(b.dY, rows, n3, b.gb2);
   // dH = dY W2 ; relu'
   if ((e = gemm(rows, H, n3, b.dY, n3, 1, L->W2, H, 1, b.dH, s)) != cudaSuccess) return e;
   relu_grad_kernel<<<grid_for((size_t)rows * H), 256, 0, s>>>(b.dH, b.Hpre, (size_t)rows * H);
   // dW1 = dH^T U ; db1 = colsum dH
-  if ((e = gemm(H, n3, rows, b.dH, 1, H, U, n3, 1, b.gW1, s)) != cudaSuccess) return e;
+  if ((e = gemm(H, n3, rows, b.dH, 1, H, U, n3, 1, b.gW1, s, b.slices)) != cudaSuccess) return e;
   colsum_kernel<<<1, 128, 0, s>>>(b.dH, rows, H, b.gb1);
   return cudaGetLastError();
 }
@@ -907,23 +939,29 @@ fe_status pcg_f32(fe_ctx* c, const float* b, float* x, int nv, const double* tol
                   cudaStream_t s);
 fe_status pcg_f32_hooked(fe_ctx* c, const float* b, float* x, int nv, const double* tol, int max_it,
                          void (*hook)(void*, int, const void*, const void*, cudaStream_t), void* user, int* its,
-                         cudaStream_t s);
+                         cudaStream_t s, int check_every);
 }
 
 namespace fe {
-// Held-out check used to pick the training checkpoint: iterations of an FP32
-// block PCG with the given preconditioner on fixed validation right-hand sides
-// (relative tolerance tol, capped at max_it).
+// Held-out data for the checkpoint choice: n_val random right-hand sides of
+// their own, solved once by FP32 Jacobi-PCG to relative tolerance 1e-7 (the
+// iteration count Jacobi needs, and x* for the held-out snapshots), with
+// snapshots (r_k, x_k) of that solve recorded every snapshot_every iterations.
 struct Validation {
   float *b = nullptr, *x = nullptr;
   int nv = 0;
   std::vector<double> tol;
+  Recorder rec;
 };
 
-static int validate(fe_ctx* c, Validation& v, int precond, int max_it, cudaStream_t s) {
+// Iterations of an FP32 block PCG with the given preconditioner on the
+// held-out right-hand sides (capped at max_it; max_it + 1 when it fails),
+// recording snapshots into rec when rec is given.
+static int validate(fe_ctx* c, Validation& v, int precond, int max_it, Recorder* rec, cudaStream_t s) {
   cudaMemsetAsync(v.x, 0, c->n_dofs * (size_t)v.nv * sizeof(float), s);
   int its = 0;
-  fe_status st = pcg_f32(c, v.b, v.x, v.nv, v.tol.data(), max_it, precond, &its, s);
+  fe_status st = rec ? pcg_f32_hooked(c, v.b, v.x, v.nv, v.tol.data(), max_it, record_hook, rec, &its, s, 4)
+                     : pcg_f32(c, v.b, v.x, v.nv, v.tol.data(), max_it, precond, &its, s);
   return st == FE_OK ? its : max_it + 1;
 }
 
@@ -974,8 +1012,12 @@ static void free_op(OpBufs& o) {
 // dL/dz is pulled back through the assembly (s_e w_i per patch entry; s_e is a
 // function of the input alone) and then through the network.  Leaves the loss
 // in tb.loss and the gradients in tb.gW1, tb.gb1, tb.gW2, tb.gb2.
+// what = kLossOnly stops after the loss; kJacobiLoss also takes the network's
+// output as zero (z = D^-1 r, the loss of plain Jacobi).
+enum { kLossAndGrads = 0, kLossOnly = 1, kJacobiLoss = 2 };
 static fe_status operator_step(fe_ctx* c, bool energy, TrainBufs& tb, OpBufs& o, const int* cells, int nv,
-                               const float* r, const float* xk, const float* xstar, cudaStream_t s) {
+                               const float* r, const float* xk, const float* xstar, cudaStream_t s,
+                               int what = kLossAndGrads) {
   LearnedPrecond* L = c->learned;
   const int n3 = L->n3;
   const size_t n = c->n_dofs, tot = n * nv;
@@ -985,14 +1027,17 @@ static fe_status operator_step(fe_ctx* c, bool energy, TrainBufs& tb, OpBufs& o,
   else col_invnorm_kernel<<<nv, 256, 0, s>>>(r, o.cs, n, nv);
   col_scale_kernel<<<grid_for(tot), 256, 0, s>>>(r, nullptr, o.cs, o.rn, tot, nv);
   if (energy) col_scale_kernel<<<grid_for(tot), 256, 0, s>>>(xk, xstar, o.cs, o.en, tot, nv);
-  gather_inputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, o.rn, nv, o.U, o.S);
-  if ((e = gemm((int)rows, kHidden, n3, o.U, n3, 1, L->W1, 1, n3, tb.Hpre, s)) != cudaSuccess) return from_cuda(e);
-  bias_act_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.Hpre, L->b1, (int)rows, kHidden, 1);
-  if ((e = gemm((int)rows, n3, kHidden, tb.Hpre, kHidden, 1, L->W2, 1, kHidden, tb.Y, s)) != cudaSuccess)
-    return from_cuda(e);
-  bias_act_kernel<<<grid_for(rows * n3), 256, 0, s>>>(tb.Y, L->b2, (int)rows, n3, 0);
+  if (what != kJacobiLoss) {
+    gather_inputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, o.rn, nv, o.U, o.S);
+    if ((e = gemm((int)rows, kHidden, n3, o.U, n3, 1, L->W1, 1, n3, tb.Hpre, s)) != cudaSuccess) return from_cuda(e);
+    bias_act_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.Hpre, L->b1, (int)rows, kHidden, 1);
+    if ((e = gemm((int)rows, n3, kHidden, tb.Hpre, kHidden, 1, L->W2, 1, kHidden, tb.Y, s)) != cudaSuccess)
+      return from_cuda(e);
+    bias_act_kernel<<<grid_for(rows * n3), 256, 0, s>>>(tb.Y, L->b2, (int)rows, n3, 0);
+  }
   jacobi_init_kernel<<<grid_for(tot), 256, 0, s>>>(o.rn, c->ws.dinv32, o.z, n, nv);
-  scatter_outputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, tb.Y, o.S, o.z, nv);
+  if (what != kJacobiLoss)
+    scatter_outputs_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, tb.Y, o.S, o.z, nv);
   const fe_mode saved = c->mode;
   c->mode = FE_FP32;
   fe_status st;
@@ -1017,14 +1062,15 @@ static fe_status operator_step(fe_ctx* c, bool energy, TrainBufs& tb, OpBufs& o,
   }
   c->mode = saved;
   if (st != FE_OK) return st;
+  if (what != kLossAndGrads) return from_cuda(cudaGetLastError());
   gather_grad_kernel<<<(unsigned)rows, 128, 0, s>>>(c->mdev, c->np, n3, cells, nv, o.q, o.S, tb.dY, nv);
-  if ((e = gemm(n3, kHidden, (int)rows, tb.dY, 1, n3, tb.Hpre, kHidden, 1, tb.gW2, s)) != cudaSuccess)
+  if ((e = gemm(n3, kHidden, (int)rows, tb.dY, 1, n3, tb.Hpre, kHidden, 1, tb.gW2, s, tb.slices)) != cudaSuccess)
     return from_cuda(e);
   colsum_kernel<<<(n3 + 127) / 128, 128, 0, s>>>(tb.dY, (int)rows, n3, tb.gb2);
   if ((e = gemm((int)rows, kHidden, n3, tb.dY, n3, 1, L->W2, kHidden, 1, tb.dH, s)) != cudaSuccess)
     return from_cuda(e);
   relu_grad_kernel<<<grid_for(rows * kHidden), 256, 0, s>>>(tb.dH, tb.Hpre, rows * kHidden);
-  if ((e = gemm(kHidden, n3, (int)rows, tb.dH, 1, kHidden, o.U, n3, 1, tb.gW1, s)) != cudaSuccess)
+  if ((e = gemm(kHidden, n3, (int)rows, tb.dH, 1, kHidden, o.U, n3, 1, tb.gW1, s, tb.slices)) != cudaSuccess)
     return from_cuda(e);
   colsum_kernel<<<1, 128, 0, s>>>(tb.dH, (int)rows, kHidden, tb.gb1);
   return from_cuda(cudaGetLastError());
@@ -1057,12 +1103,33 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
     st = from_cuda(e);
   }
   int val_jac = 0, best_its = 0, best_epoch = 0;
-  if (st == FE_OK && val.nv > 0) {
-    val_jac = validate(c, val, FE_PRECOND_JACOBI, 100000, s);
+  float val_loss_jac = 0.f, best_loss = 0.f, last_loss = 0.f;
+  // mean loss of the live network (or of Jacobi) over the held-out snapshots
+  auto held_out_loss = [&](int what, float& out) -> fe_status {
+    double sum = 0.0;
+    for (int k = 0; k < val.rec.count; ++k) {
+      fe_status q = operator_step(c, energy, tb, ob, cells, val.nv, val.rec.r[k], val.rec.x[k], val.x, s, what);
+      if (q != FE_OK) return q;
+      float h = 0.f;
+      cudaMemcpyAsync(&h, tb.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+      cudaError_t ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) return from_cuda(ce);
+      sum += h;
+    }
+    out = val.rec.count ? (float)(sum / val.rec.count) : 0.f;
+    return FE_OK;
+  };
+  const bool use_val = st == FE_OK && val.nv > 0;
+  if (use_val) {
+    // the Jacobi solve of the held-out right-hand sides: iterations to beat,
+    // x* and the held-out snapshots
+    val_jac = validate(c, val, FE_PRECOND_JACOBI, 100000, &val.rec, s);
     best_its = val_jac;
     copy_weights(L, best.W1, best.b1, best.W2, best.b2, true, s);
     cudaMemsetAsync(best.W2, 0, wsz * sizeof(float), s);
     cudaMemsetAsync(best.b2, 0, n3 * sizeof(float), s);
+    st = held_out_loss(kJacobiLoss, val_loss_jac);
+    best_loss = val_loss_jac;
   }
   float first = 0.f, last = 0.f, ep_first = 0.f;
   int step = 0;
@@ -1087,17 +1154,57 @@ static fe_status train_operator_loss(fe_ctx* c, const fe_train_desc* d, Recorder
     if (e != cudaSuccess && st == FE_OK) st = from_cuda(e);
     last = per_epoch ? ep_loss / per_epoch : 0.f;
     if (ep == 0) ep_first = last;
-    if (st == FE_OK && val.nv > 0) {
-      if ((e = refresh_images(c, s)) != cudaSuccess) { st = from_cuda(e); break; }
-      const int its = validate(c, val, FE_PRECOND_LEARNED, 2 * val_jac + 10, s);
-      if (its < best_its) {
-        best_its = its;
+    if (st == FE_OK && use_val) {
+      float lv = 0.f;
+      st = held_out_loss(kLossOnly, lv);
+      last_loss = lv;
+      if (st == FE_OK && lv < best_loss) {
+        best_loss = lv;
         best_epoch = ep + 1;
         copy_weights(L, best.W1, best.b1, best.W2, best.b2, true, s);
       }
     }
   }
-  if (st == FE_OK && val.nv > 0) copy_weights(L, best.W1, best.b1, best.W2, best.b2, false, s);
+  if (st == FE_OK && use_val) {
+    // Candidates, in this order: the epoch of the lowest held-out loss and the
+    // last epoch.  The first that needs fewer iterations than Jacobi in one
+    // held-out solve is kept; if none does, the zero output layer (Jacobi).
+    Checkpoint lastw;
+    e = cudaMalloc(&lastw.W1, wsz * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&lastw.b1, kHidden * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&lastw.W2, wsz * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&lastw.b2, n3 * sizeof(float));
+    if (e != cudaSuccess) st = from_cuda(e);
+    if (st == FE_OK) copy_weights(L, lastw.W1, lastw.b1, lastw.W2, lastw.b2, true, s);
+    const int last_epoch = d->epochs;
+    int cand[2] = {best_epoch, last_epoch != best_epoch ? last_epoch : 0};
+    bool kept = false;
+    for (int ci = 0; ci < 2 && st == FE_OK && !kept; ++ci) {
+      if (cand[ci] <= 0) continue;
+      const Checkpoint& w = cand[ci] == best_epoch ? best : lastw;
+      copy_weights(L, w.W1, w.b1, w.W2, w.b2, false, s);
+      if ((e = refresh_images(c, s)) != cudaSuccess) { st = from_cuda(e); break; }
+      const int its = validate(c, val, FE_PRECOND_LEARNED, 2 * val_jac + 10, nullptr, s);
+      if (its < val_jac) {
+        kept = true;
+        best_its = its;
+        if (cand[ci] != best_epoch) best_loss = last_loss;
+        best_epoch = cand[ci];
+      }
+    }
+    if (st == FE_OK && !kept) {
+      copy_weights(L, best.W1, best.b1, best.W2, best.b2, false, s);
+      cudaMemsetAsync(L->W2, 0, wsz * sizeof(float), s);
+      cudaMemsetAsync(L->b2, 0, n3 * sizeof(float), s);
+      best_epoch = 0;
+      best_its = val_jac;
+      best_loss = val_loss_jac;
+    }
+    cudaStreamSynchronize(s);
+    for (float* p : {lastw.W1, lastw.b1, lastw.W2, lastw.b2}) cudaFree(p);
+  }
+  inf->val_loss_jacobi = val_loss_jac;
+  inf->val_loss_kept = best_loss;
   inf->val_jacobi_iterations = val_jac;
   inf->val_learned_iterations = best_its;
   inf->best_epoch = best_epoch;
@@ -1227,7 +1334,7 @@ extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_trai
       for (int j = 0; j < nv; ++j) bn[j] += (double)hb[i * nv + j] * hb[i * nv + j];
     for (int j = 0; j < nv; ++j) tol[j] = d->traj_rtol * std::sqrt(bn[j]);
     int its = 0;
-    st = pcg_f32_hooked(c, b, x, nv, tol.data(), 200000, record_hook, &rec, &its, s);
+    st = pcg_f32_hooked(c, b, x, nv, tol.data(), 200000, record_hook, &rec, &its, s, 8);
     inf.trajectory_iterations = its;
   }
   const bool patch_mode = d->objective == FE_TRAIN_PATCH_ERROR;
@@ -1254,11 +1361,25 @@ extern "C" fe_status fe_precond_train(fe_ctx* c, const fe_train_desc* d, fe_trai
     e = cudaMalloc(&val.b, hv.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&val.x, hv.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(val.b, hv.data(), hv.size() * sizeof(float), cudaMemcpyHostToDevice);
+    // held-out snapshots: up to four, spread over the iterations the training
+    // snapshots span
+    val.rec.max_snap = std::min(d->snapshots, 4);
+    val.rec.every = d->snapshot_every * std::max(1, d->snapshots / 4);
+    val.rec.tot = hv.size();
+    for (int k = 0; k < val.rec.max_snap && e == cudaSuccess; ++k) {
+      float *pr = nullptr, *px = nullptr;
+      e = cudaMalloc(&pr, hv.size() * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc(&px, hv.size() * sizeof(float));
+      val.rec.r.push_back(pr);
+      val.rec.x.push_back(px);
+    }
     if (e != cudaSuccess) st = from_cuda(e);
   }
   if (st == FE_OK && !patch_mode) st = train_operator_loss(c, d, rec, cells, nv, &inf, s, x, val);
   cudaFree(val.b);
   cudaFree(val.x);
+  for (float* p : val.rec.r) cudaFree(p);
+  for (float* p : val.rec.x) cudaFree(p);
   // patch regression: U = R_e r_k / s, T = HF(R_e (x* - x_k - D^-1 r_k)) / s
   Gll gll{};
   for (int i = 0; i < c->np && i < 16; ++i) gll.x[i] = (float)c->gll[i];

@@ -29,7 +29,7 @@ using namespace fe;
 namespace {
 
 fe_status from_cuda(cudaError_t e) {
-  return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
+  return fe::cuda_status(e);
 }
 
 constexpr long long kV = 0, kC = 1, kF = 2;

@@ -271,7 +271,7 @@ void build_gll_mass(fe_ctx* c) {
 
 using namespace fe;
 
-static fe_status from_cuda(cudaError_t e) { return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA); }
+static fe_status from_cuda(cudaError_t e) { return fe::cuda_status(e); }
 
 extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_desc* quad, double mu, fe_ctx** out) {
   if (!out) return FE_EINVAL;
@@ -338,6 +338,9 @@ extern "C" fe_status fe_setup(const fe_mesh_desc* mesh, int p, const fe_quad_des
                             {0, 0, (X[4][2] - X[0][2]) / 2}};
           double G[6];
           const double det = metric(J, mu, G);
+          // an axis-aligned box: the metric is diagonal, which the cell
+          // kernels without per-point geometry rely on
+          if (G[1] != 0.0 || G[2] != 0.0 || G[4] != 0.0) bad = true;
           for (int k = 0; k < 6; ++k) c->cellG[e * 6 + k] = G[k];
           for (size_t Q = 0; Q < nq3; ++Q) c->detJ[e * nq3 + Q] = det;
         } else {

@@ -463,7 +463,7 @@ using namespace fe;
 namespace {
 
 fe_status from_cuda(cudaError_t e) {
-  return e == cudaSuccess ? FE_OK : (e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA);
+  return fe::cuda_status(e);
 }
 
 template <typename T>
@@ -656,12 +656,12 @@ fe_status true_residual(fe_ctx* c, const double* B, const double* X, int nv, dou
 }
 
 fe_status pcg_f32_hooked(fe_ctx* c, const float* b, float* x, int nv, const double* tol, int max_it, PcgHook hook,
-                         void* user, int* its, cudaStream_t s) {
+                         void* user, int* its, cudaStream_t s, int check_every) {
   SolveWs& w = c->ws;
   const fe_mode saved = c->inner_mode;
   c->inner_mode = FE_FP32;
   fe_status st = pcg<float>(c, b, x, nv, tol, max_it, FE_PRECOND_JACOBI, s, w.v32[0], w.v32[1], w.v32[2], w.v32[5],
-                            its, 8, hook, user);
+                            its, check_every, hook, user);
   c->inner_mode = saved;
   return st;
 }

@@ -28,7 +28,13 @@ MODES = {"fp64": FE_FP64, "fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16, "tf
 class FeError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {status_str(status)} ({status})")
+        detail = ""
+        if status in (2, 3):   # FE_ENOMEM, FE_ECUDA: name the CUDA runtime error behind it
+            try:
+                detail = f" [{lib().fe_last_cuda_error().decode()}]"
+            except Exception:
+                pass
+        super().__init__(f"{what}: {status_str(status)} ({status}){detail}")
 
 
 class fe_mesh_desc(ctypes.Structure):
@@ -63,7 +69,7 @@ class fe_train_info(ctypes.Structure):
                 ("loss_first_step", ctypes.c_float), ("loss_first_epoch", ctypes.c_float),
                 ("loss_last_epoch", ctypes.c_float), ("seconds", ctypes.c_double),
                 ("val_jacobi_iterations", ctypes.c_int), ("val_learned_iterations", ctypes.c_int),
-                ("best_epoch", ctypes.c_int)]
+                ("best_epoch", ctypes.c_int), ("val_loss_jacobi", ctypes.c_float), ("val_loss_kept", ctypes.c_float)]
 
 
 class fe_batch_info(ctypes.Structure):
@@ -129,6 +135,7 @@ def lib() -> ctypes.CDLL:
         "fe_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.POINTER(fe_solve_info), _DP, _VP]),
         "fe_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+        "fe_last_cuda_error": (ctypes.c_char_p, []),
         "fe_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "fe_precond_init": (ctypes.c_int, [_VP, ctypes.c_ulonglong]),
         "fe_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(ctypes.c_int),

@@ -46,6 +46,13 @@ def test_status_strings(libfe):
     assert fe.status_str(99) == "unknown status"
 
 
+def test_last_cuda_error_name(libfe):
+    """The name of the CUDA error behind the last FE_ECUDA / FE_ENOMEM of this
+    thread: "none" or a CUDA runtime error name, never a null pointer."""
+    name = libfe.fe_last_cuda_error().decode()
+    assert name == "none" or name.startswith("cuda"), name
+
+
 @pytest.mark.parametrize("kw,status", [
     (dict(nx=0, ny=2, nz=2, p=2, n_q=4), 1),                       # no cells
     (dict(nx=2, ny=2, nz=2, p=9, n_q=11), 8),                      # degree outside the compiled set

@@ -260,3 +260,64 @@ def test_small_mesh_path_bitwise(fe, mode, case):
         _compare(Ys.double().cpu().numpy(), Yref, TOL[mode])
     finally:
         fe.fe_destroy(ctx)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "bf16"])
+def test_two_host_threads_own_contexts(fe, mode):
+    """Two host threads each set up their own context on device 0 and run
+    products on their own streams at the same time.  The launches need more
+    than 48 KB of dynamic shared memory (the 3x2x3 p=6 periodic mesh with 64
+    vectors), whose attribute is set once per device and kernel under a lock;
+    each thread's results must equal the same product run alone, bit for bit."""
+    import threading
+
+    nx, ny, nz, p, nq = 3, 2, 3, 6, 8
+    n_vec = 64
+    ctx0, _, _ = _setup_pair(fe, nx, ny, nz, p, nq, periodic=True, seed=31)
+    try:
+        fe.fe_set_mode(ctx0, mode)
+        dt = torch.float64 if mode == "fp64" else torch.float32
+        n = fe.fe_num_dofs(ctx0)
+        Xs = [torch.from_numpy(inputs.random_block(n, n_vec, "normal", 40 + k)).to(device="cuda", dtype=dt)
+              for k in range(2)]
+        ref = []
+        for X in Xs:
+            Y = torch.full_like(X, float("nan"))
+            fe.fe_apply(ctx0, X, Y)
+            ref.append(Y)
+        torch.cuda.synchronize()
+    finally:
+        fe.fe_destroy(ctx0)
+
+    out = [None, None]
+    errors = []
+    barrier = threading.Barrier(2)
+
+    def worker(k):
+        try:
+            torch.cuda.set_device(0)
+            ctx, _, _ = _setup_pair(fe, nx, ny, nz, p, nq, periodic=True, seed=31)
+            try:
+                fe.fe_set_mode(ctx, mode)
+                s = torch.cuda.Stream()
+                with torch.cuda.stream(s):
+                    Y = torch.full_like(Xs[k], float("nan"))
+                barrier.wait(timeout=60)
+                for _ in range(5):
+                    fe.fe_apply(ctx, Xs[k], Y, stream=s)
+                s.synchronize()
+                out[k] = Y
+            finally:
+                fe.fe_destroy(ctx)
+        except Exception as ex:  # reported on the main thread
+            errors.append(repr(ex))
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    for k in range(2):
+        assert out[k] is not None
+        assert torch.equal(out[k], ref[k])
