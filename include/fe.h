@@ -69,7 +69,13 @@ typedef enum { FE_QUAD_GAUSS = 0, FE_QUAD_GLL = 1 } fe_quad_kind;
  * value an unevaluated sum of two floats, ~48 significant bits; error-free
  * sums and products, compensated dot products) on the FP32 pipe, which
  * GB300 runs at 64 times its FP64 rate; errors stay within the FP64 bound
- * (1e-12 relative).  FE_BF16S: as FE_BF16, but X and Y are bfloat16 in
+ * (1e-12 relative).  Both parts of a double-float value are floats, so the
+ * mode has FP32's exponent range: X, the potential and the results must stay
+ * below ~3.4e38 in magnitude (larger values overflow to infinity), and a
+ * value below ~1e-31 in magnitude keeps fewer than 48 significant bits (its
+ * low part falls into the subnormal range; below ~1e-38 the high part does
+ * too), so blocks with entries that small relative to FP64's range lose the
+ * FP64-level accuracy; FE_FP64 has no such limit.  FE_BF16S: as FE_BF16, but X and Y are bfloat16 in
  * device memory (half the bytes of FE_BF16); the colour-ordered accumulation
  * of Y rounds to bfloat16 after every add.  FE_TF32, FE_BF16 and FE_BF16S run
  * on the tcgen05 tensor cores (operands in shared memory, FP32 accumulators in
