@@ -395,3 +395,51 @@ def test_row_block_assembly_equals_full_assembly(periodic, distorted):
     np.testing.assert_array_equal(B.toarray(), A[rows].toarray())
     X = np.random.default_rng(2).normal(size=(orc.num_dofs(mesh, p), 5))
     np.testing.assert_allclose(orc.spmm(B, X), orc.apply_rows(mesh, p, nq, X, rows, Vq=V), rtol=1e-13, atol=1e-13)
+
+
+def _gll_nodes_numpy(p):
+    """GLL nodes from numpy alone: the end points and the roots of P_p'."""
+    inner = np.polynomial.legendre.Legendre.basis(p).deriv().roots().real
+    return np.concatenate([[-1.0], np.sort(inner), [1.0]])
+
+
+def _lagrange_by_vandermonde(nodes, t):
+    """Values and first derivatives at the points t of the Lagrange basis on
+    `nodes`, from the monomial coefficients (inverse Vandermonde matrix);
+    rows are points, columns basis functions."""
+    n = len(nodes)
+    C = np.linalg.inv(np.vander(nodes, n, increasing=True))
+    T = np.vander(t, n, increasing=True)
+    dT = np.zeros_like(T)
+    dT[:, 1:] = T[:, :-1] * np.arange(1, n)
+    return T @ C, dT @ C
+
+
+@pytest.mark.parametrize("p,nq", [(2, 4), (3, 5), (4, 6)])
+def test_box_cell_matrix_is_a_kronecker_sum(p, nq):
+    """On an axis-aligned box cell J = diag(h/2) is diagonal, and so is the
+    metric mu det J J^-1 J^-T: the cell matrix (Sec. 2.2, the cell stiffness
+    and mass by the tensor quadrature) separates into
+        mu det J sum_d (2/h_d)^2 K^ (x) M^ (x) M^ (K^ along direction d)
+        + c det J M^ (x) M^ (x) M^              (V = c constant)
+    with the 1D matrices K^ = D^T W D and M^ = N^T W N of the reference
+    interval, built here from numpy's Gauss rule and a Vandermonde Lagrange
+    basis on numpy's GLL nodes.  No mixed d/dx d/dy term appears: this is the
+    reading the CUDA-core kernels use for box cells (three scalings of the
+    gradient at every quadrature point)."""
+    mu, c = 0.5, 1.7
+    lo, hi = (0.1, -0.2, 0.3), (0.6, 0.5, 0.55)
+    h = [hi[d] - lo[d] for d in range(3)]
+    mesh = orc.Mesh(1, 1, 1, lo=lo, hi=hi)
+    Vq = np.full(nq ** 3, c)
+    A = orc.cell_matrix(mesh, p, nq, orc.GAUSS, mu, Vq, 0)
+
+    xq, wq = np.polynomial.legendre.leggauss(nq)
+    N, D = _lagrange_by_vandermonde(_gll_nodes_numpy(p), xq)
+    M1 = N.T @ (wq[:, None] * N)
+    K1 = D.T @ (wq[:, None] * D)
+    det = h[0] * h[1] * h[2] / 8.0
+    kron3 = lambda a3, a2, a1: np.kron(a3, np.kron(a2, a1))   # local index i1 + n_p (i2 + n_p i3)
+    ref = mu * det * ((2 / h[0]) ** 2 * kron3(M1, M1, K1) + (2 / h[1]) ** 2 * kron3(M1, K1, M1)
+                      + (2 / h[2]) ** 2 * kron3(K1, M1, M1)) + c * det * kron3(M1, M1, M1)
+    assert np.abs(A - ref).max() <= 1e-12 * np.abs(ref).max()
