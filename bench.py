@@ -674,7 +674,8 @@ def df64_batch_subprocess(ms_fp64_batch: float) -> dict:
                            text=True, timeout=900, env=env, cwd=ROOT)
         lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
         if r.returncode != 0 or not lines:
-            return {"error": f"child exited {r.returncode}: {r.stderr.strip().splitlines()[-1:] }"}
+            tail = r.stderr.strip().splitlines()
+            return {"error": f"child exited {r.returncode}: {tail[-1] if tail else 'no output'}"}
         d = json.loads(lines[-1])
         d["speedup_vs_fp64_batch"] = ms_fp64_batch / d["ms_per_batch_apply"]
         return d
